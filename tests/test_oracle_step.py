@@ -1,0 +1,254 @@
+"""Pins of the oracle's pointwise step (sections 3.1, 3.3, 3.4, 4, 5):
+staggered-difference exactness (Eq. 31), summation by parts between the
+corner divergence and the cell gradient, the STZ rate against the Eq. (21)
+form evaluated in high precision, the 0-D reduction of a whole step under
+uniform simple shear, conservation and continuum consistency of the chi
+diffusion term, and the wall velocity profiles with their printed constants."""
+import json
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1904_03808_gb300 import inputs as I
+
+MU = I.TABLE1["mu"]
+LAM = I.lame_lambda(I.TABLE1["K"], MU)
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def stz(l=1e-4):
+    return O.STZ(**I.stz_values(l))
+
+
+def test_cell_gradient_exact_on_trilinear():
+    rng = np.random.default_rng(1)
+    nx, ny, nz, h = 8, 6, 5, 0.3
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny), np.arange(nx), indexing="ij")
+    X, Y, Z = i * h, j * h, k * h
+    c = rng.normal(size=(3, 8))
+    def f(a, X, Y, Z):
+        return (c[a, 0] + c[a, 1] * X + c[a, 2] * Y + c[a, 3] * Z + c[a, 4] * X * Y +
+                c[a, 5] * X * Z + c[a, 6] * Y * Z + c[a, 7] * X * Y * Z)
+    v = np.stack([f(a, X, Y, Z) for a in range(3)])
+    L = O.cell_gradient(v, h)
+    kc, jc, ic = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    Xc, Yc, Zc = (ic + 0.5) * h, (jc + 0.5) * h, (kc + 0.5) * h
+    sl = (slice(None), slice(0, ny - 1), slice(0, nx - 1))  # away from the periodic seam
+    for a in range(3):
+        dx = c[a, 1] + c[a, 4] * Yc + c[a, 5] * Zc + c[a, 7] * Yc * Zc
+        dy = c[a, 2] + c[a, 4] * Xc + c[a, 6] * Zc + c[a, 7] * Xc * Zc
+        dz = c[a, 3] + c[a, 5] * Xc + c[a, 6] * Yc + c[a, 7] * Xc * Yc
+        for b, want in enumerate((dx, dy, dz)):
+            assert np.allclose(L[..., a, b][sl], want[sl], rtol=1e-12, atol=1e-12)
+
+
+def test_divergence_is_minus_gradient_transpose():
+    """sum_corners v . div(sigma) = - sum_cells sigma : grad(v) for v with zero
+    walls: the corner divergence and the Eq. (31) cell gradient are negative
+    adjoints, which pins both index conventions."""
+    rng = np.random.default_rng(2)
+    nx, ny, nz, h, dt = 6, 8, 4, 0.7, 1.3
+    v = rng.normal(size=(3, nz + 1, ny, nx))
+    v[:, 0] = 0
+    v[:, nz] = 0
+    sig = rng.normal(size=(6, nz, ny, nx))
+    b = O.div_rhs(sig, h, dt, MU) * (MU * dt / (h * h))  # undo the system scaling
+    lhs = np.sum(v * b)
+    L = O.cell_gradient(v, h)
+    full = np.zeros((nz, ny, nx, 3, 3))
+    comp = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (1, 2): 3, (2, 1): 3, (0, 2): 4, (2, 0): 4,
+            (0, 1): 5, (1, 0): 5}
+    for (a, bb), q in comp.items():
+        full[..., a, bb] = sig[q]
+    rhs = -np.sum(full * L)
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs))
+
+
+@pytest.mark.parametrize("sbar_gpa,chi", [(0.9, 600.0), (1.2, 600.0), (1.5, 600.0), (1.2, 690.0),
+                                          (1.5, 900.0), (0.9, 900.0), (3.0, 450.0)])
+def test_stz_rate_against_eq21_form(sbar_gpa, chi):
+    """Eqs. (20)-(22): the oracle's cosh form equals C = (R(+s) + R(-s))/2 with
+    R(+-s) = exp(-(Delta -+ Omega eps0 s)/(kB T)), evaluated here with 40 digits."""
+    p = I.stz_values(1e-4)
+    mp.mp.dps = 40
+    s = mp.mpf(sbar_gpa) * mp.mpf(10) ** 9
+    kT = mp.mpf(p["kB"]) * p["T"]
+    dE = mp.mpf(p["Delta_K"]) * mp.mpf(p["kB"])
+    b = mp.mpf(p["Omega"]) * p["eps0"] * s
+    C = (mp.e ** (-(dE - b) / kT) + mp.e ** (-(dE + b) / kT)) / 2
+    want = mp.e ** (-mp.mpf(p["ez_K"]) / chi) * C * (1 - mp.mpf(p["sY"]) / s) / p["tau0"]
+    got = O.dpl(stz(), sbar_gpa * 1e9, chi)
+    assert abs(got - float(want)) <= 1e-12 * float(want)
+
+
+def test_stz_rate_yield_and_chi_scaling():
+    p = stz()
+    assert O.dpl(p, 0.85e9, 600.0) == 0.0
+    assert O.dpl(p, 0.5e9, 900.0) == 0.0
+    assert O.dpl(p, 1.2e9, 0.0) == 0.0
+    r = O.dpl(p, 1.3e9, 650.0) / O.dpl(p, 1.3e9, 600.0)
+    assert abs(r - math.exp(21000.0 * (1 / 600.0 - 1 / 650.0))) < 1e-12 * r
+
+
+def _zero_d_reference(sig0, chi0, U_prev, U_next, H, dt, p):
+    """One step of the per-cell ODE that the whole 3-D step reduces to when
+    chi and sigma are uniform under simple shear: L = dv_x/dz = 2U/H in the
+    (x, z) slot; Eq. (27) then Eq. (29) with D^{n+1} from U_next; Eq. (26)
+    without diffusion (uniform fields)."""
+    s = sig0
+    Lm = np.zeros((3, 3))
+    Lm[0, 2] = 2.0 * U_prev / H
+    tr3 = np.trace(s) / 3.0
+    s0 = s - tr3 * np.eye(3)
+    sb = math.sqrt(0.5 * np.sum(s0 * s0))
+    D = 0.0
+    if sb > p["sY"]:
+        kT = p["kB"] * p["T"]
+        D = math.exp(-p["ez_K"] / chi0) * math.exp(-p["Delta_K"] / p["T"]) * \
+            math.cosh(p["Omega"] * p["eps0"] * sb / kT) * (1 - p["sY"] / sb) / p["tau0"]
+    plastic = (2 * MU * D / sb) * s0 if D > 0 else 0.0
+    star = s + dt * (Lm @ s + s @ Lm.T - np.trace(Lm) * s - plastic)
+    Dn = np.zeros((3, 3))
+    Dn[0, 2] = Dn[2, 0] = U_next / H
+    new = star + dt * (LAM * np.trace(Dn) * np.eye(3) + 2 * MU * Dn)
+    chi1 = chi0 + dt / p["c0"] * (2 * D * sb / p["sY"]) * (p["chi_inf"] - chi0)
+    return new, chi1
+
+
+@pytest.mark.parametrize("preload", [0.0, 1.5e9])
+def test_step_reduces_to_zero_d_under_uniform_shear(preload):
+    n, steps = 8, 4
+    w = I.Workload(n, steps=steps, strain=0.02, preload=preload)
+    p = I.stz_values(w.h)
+    v, sig, _, t = w.initial_state()
+    chi = np.full((n, n, n), 640.0)
+    mg = O.MG(n, n, n, LAM, MU)
+    bc = O.BC(**w.bc_values())
+    s_ref = np.zeros((3, 3))
+    s_ref[0, 2] = s_ref[2, 0] = preload
+    c_ref = 640.0
+    def U(tt):
+        return w.U_B * min(tt / w.t_ramp, 1.0)
+    for _ in range(steps):
+        st, cyc, hist = O.qs_step(mg, v, sig, chi, w.h, w.dt, LAM, MU, O.STZ(**p), bc, t,
+                                  tol=1e-13, max_cycles=200)
+        assert st == 0
+        s_ref, c_ref = _zero_d_reference(s_ref, c_ref, U(t), U(t + w.dt), w.H, w.dt, p)
+        t += w.dt
+        zk = (np.arange(n + 1) - n / 2.0) * w.h
+        v_lin = 2.0 * U(t) / w.H * zk
+        assert np.allclose(v[0], v_lin[:, None, None], rtol=0, atol=1e-10 * abs(U(t)))
+        assert np.allclose(v[1:], 0.0, atol=1e-10 * abs(U(t)))
+        comp = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+        scale = max(np.abs(s_ref).max(), 1.0)
+        for q, (a, b) in enumerate(comp):
+            assert np.allclose(sig[q], s_ref[a, b], rtol=0, atol=1e-9 * scale), (q, sig[q].ravel()[:2], s_ref[a, b])
+        assert np.allclose(chi, c_ref, rtol=1e-13)
+    if preload:
+        assert c_ref > 640.0  # plasticity was active
+
+
+def _x_wave_state(n, amp=20.0):
+    h = 1e-4
+    sig = np.zeros((6, 4, 4, n))
+    sig[4] = 1.6e9
+    x = (np.arange(n) + 0.5) / n
+    chi = np.broadcast_to(650.0 + amp * np.sin(2 * np.pi * x), (4, 4, n)).copy()
+    return h, sig, chi, x
+
+
+def test_chi_diffusion_conserves_in_periodic_direction():
+    p = stz(l=2e-4)
+    n = 32
+    h, sig, chi, _ = _x_wave_state(n)
+    v = np.zeros((3, 5, 4, n))
+    dt = 1e-6
+    ss, D, sb = O.stress_star(v, sig, chi, h, dt, MU, p)
+    new = O.chi_update(sig, chi, D, sb, h, dt, p)
+    growth = dt / p.c0 * (2 * D * sb / p.sY) * (p.chi_inf - chi)
+    diff = new - chi - growth
+    row = diff[1, 1]
+    # rounding of chi' - chi is ~eps * chi per cell; the telescoping sum is zero
+    assert abs(row.sum()) <= 8 * np.finfo(float).eps * np.abs(chi).max() * n
+    assert abs(row.sum()) <= 1e-8 * np.abs(row).sum()
+    assert np.abs(row).max() > 0
+
+
+def test_chi_diffusion_second_order_in_x():
+    """l^2 d/dx(D dchi/dx) for chi = 650 + 20 sin(2 pi x/X), uniform stress:
+    the discrete term converges at second order to the closed form
+    l^2 (D' chi_x^2 + D chi_xx), D' = D e_z / chi^2."""
+    p = stz()
+    errs = []
+    for n in (32, 64, 128):
+        h, sig, chi, x = _x_wave_state(n)
+        X = n * h
+        p.l = 3e-5
+        v = np.zeros((3, 5, 4, n))
+        dt = 1e-6
+        ss, D, sb = O.stress_star(v, sig, chi, h, dt, MU, p)
+        new = O.chi_update(sig, chi, D, sb, h, dt, p)
+        growth = dt / p.c0 * (2 * D * sb / p.sY) * (p.chi_inf - chi)
+        term = (new - chi - growth)[1, 1] * p.c0 / dt
+        c = chi[1, 1]
+        cx = 20.0 * 2 * np.pi / X * np.cos(2 * np.pi * x)
+        cxx = -20.0 * (2 * np.pi / X) ** 2 * np.sin(2 * np.pi * x)
+        Dx = D[1, 1]
+        want = p.l ** 2 * (Dx * p.ez_K / c ** 2 * cx ** 2 + Dx * cxx)
+        errs.append(np.abs(term - want).max() / np.abs(want).max())
+    assert abs(np.log2(errs[0] / errs[1]) - 2) < 0.15 and abs(np.log2(errs[1] / errs[2]) - 2) < 0.15, errs
+
+
+def test_simple_shear_walls_and_ramp():
+    n = 8
+    v = np.zeros((3, n + 1, n, n))
+    bc = O.BC(kind=0, U_B=2.0, t_ramp=4.0, omega=0, R=0, lambda_w=0)
+    O.wall_fill(v, 0.1, bc, 1.0)
+    assert np.all(v[0, n] == 0.5) and np.all(v[0, 0] == -0.5) and np.all(v[1:, [0, n]] == 0)
+    O.wall_fill(v, 0.1, bc, 9.0)
+    assert np.all(v[0, n] == 2.0) and np.all(v[0, 0] == -2.0)
+
+
+def test_disc_walls_rotation():
+    """Section 5: a rotation inside r < R with a smooth exp(-lambda_w (r^2-R^2)^2)
+    cutoff; the printed choice of lambda_w leaves 10% of the angular velocity a
+    quarter of the way from the disc edge to the domain edge."""
+    g = json.load(open(os.path.join(GOLD, "paper_constants.json")))
+    R = g["disc_R"]["value"]
+    lam_w = 16 * math.log(10) / (1 - R * R) ** 2
+    r2q = R * R + (1 - R * R) / 4
+    assert abs(math.exp(-lam_w * (r2q - R * R) ** 2) - g["disc_quarter_way_fraction"]["value"]) < 1e-12
+    n, h, om = 24, 1.0 / 12, 0.7
+    v = np.zeros((3, n + 1, n, n))
+    for kind, sgn in ((1, 0.0), (2, 1.0), (3, -1.0)):
+        O.wall_fill(v, h, O.BC(kind=kind, U_B=0, t_ramp=1, omega=om, R=R, lambda_w=lam_w), 0.0)
+        Lh = n * h / 2
+        x = -Lh + np.arange(n) * h
+        X, Y = np.meshgrid(x, x, indexing="xy")
+        top = v[:, n]
+        assert np.allclose(top[0] * X + top[1] * Y, 0.0, atol=1e-15)  # tangential
+        r2 = (X ** 2 + Y ** 2) / Lh ** 2
+        speed = np.hypot(top[0], top[1])
+        inside = r2 < R * R
+        assert np.allclose(speed[inside], om * np.sqrt(X ** 2 + Y ** 2)[inside], rtol=1e-14)
+        f = speed[~inside] / (om * np.sqrt(X ** 2 + Y ** 2)[~inside])
+        assert np.all(f <= 1) and np.all(f >= 0) and f.min() < 1e-30
+        assert np.all(top[2] == 0)
+        assert np.allclose(v[:, 0], sgn * top, atol=0)
+
+
+def test_printed_constants():
+    """Table 1 and section 4: c_s = sqrt(mu/rho) = 2.47 km/s, t_s = L/c_s = 4.05 us."""
+    g = json.load(open(os.path.join(GOLD, "paper_constants.json")))
+    cs = math.sqrt(g["mu"]["value"] / g["rho"]["value"])
+    assert round(cs / 1000, 2) == g["c_s_km_per_s"]["value"]
+    ts = g["L"]["value"] / cs
+    assert round(ts * 1e6, 2) == g["t_s_us"]["value"]
+    assert abs(I.shear_time_unit() - ts) < 1e-18
+    for key in ("K", "mu", "rho", "sY", "tau0", "eps0", "c0", "Delta_K", "T", "chi_inf", "ez_K"):
+        assert I.TABLE1[key] == g[key]["value"], key
+    assert abs(I.TABLE1["Omega"] - g["Omega_A3"]["value"] * 1e-30) < 1e-40
