@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the quasi-static projection step on GB300.
+
+One step = one qs_step call: stress/STZ predictor, chi update, wall fill,
+right-hand side, multigrid solve of the projection system to relative
+residual 1e-10 (warm-started), stress correction.  Workload: 256^3 cells,
+simple shear with an STZ-active preload, seeded Gaussian chi field (600 K,
+30 K, correlation length 4 cells), mixed precision (FP32 V-cycles inside FP64
+iterative refinement).  The same steps in plain FP64 and a cold solve of a
+random right-hand side are timed beside it.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("sec per multigrid solve (rel resid 1e-10) at 256³, mixed vs FP64; "
+          "smoother HBM GB/s")
+UNIT = "s/solve"
+TOL = 1e-10
+PRELOAD = 1.2e9       # Pa, uniform sigma_xz at t0: keeps the STZ rate active
+INNER = 4             # FP32 V-cycles per refinement step
+SMOOTH_BYTES = 36     # algorithmic bytes per node per FP32 sweep: read v, b; write v (9 floats)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--inner", type=int, default=INNER)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_1904_03808_gb300 import inputs as I
+    return I.Workload(n, steps=50, strain=0.02, preload=PRELOAD, chi_mean=600.0, chi_std=30.0,
+                      lc_cells=4.0, seed=3)
+
+
+def config(w, extra=None):
+    c = {"workload": "simple shear %dx%dx%d cells, STZ-active (sigma_xz0 = %.1f GPa), chi0 seeded "
+                     "Gaussian field 600 K / 30 K / l_c = 4 cells, dt = 200 t_s, warm-started "
+                     "solves to rel. resid 1e-10" % (w.nx, w.ny, w.nz, PRELOAD / 1e9),
+         "grid": [w.nx, w.ny, w.nz], "unknowns": 3 * w.nx * w.ny * (w.nz - 1),
+         "l2": "inputs larger than L2 (state 1.3 GB, hierarchy 2+ GB)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms",
+                 "100", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_per_sweep(n_nodes):
+    """DRAM bytes per finest-level sweep from the committed ncu summary, scaled
+    by node count, or None when the smoother source changed since capture."""
+    p = os.path.join(ROOT, "profiles", "smoother_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1904_03808_gb300", "csrc", d["source"]), "rb").read()
+    if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+        return None
+    return d["dram_bytes_per_node_per_sweep"] * n_nodes
+
+
+# --------------------------------------------------------------------- oracle
+
+def oracle_sample(w, v, sig, chi, t, cycles_per_solve):
+    """Time the FP64 CPU oracle on a bounded sample of the same workload:
+    the pointwise step pieces at full size, one V-cycle and one residual norm;
+    per-solve seconds = pointwise + cycles_per_solve * (V-cycle + residual)."""
+    import oracle as O
+    lam, mu = w.lam, w.mu
+    p = O.STZ(**w.stz)
+    mg = O.MG(w.nx, w.ny, w.nz, lam, mu)
+    v = v.copy()
+    t0 = time.perf_counter()
+    ss, D, sb = O.stress_star(v, sig, chi, w.h, w.dt, mu, p)
+    O.chi_update(sig, chi, D, sb, w.h, w.dt, p)
+    O.wall_fill(v, w.h, O.BC(**w.bc_values()), t + w.dt)
+    b = O.div_rhs(ss, w.h, w.dt, mu)
+    O.stress_final(v, ss, w.h, w.dt, lam, mu)
+    t_pw = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mg.vcycle(b, v)
+    r = O.residual(mg.stencil(0), b, v)
+    O.norm2(r)
+    t_cyc = time.perf_counter() - t0
+    mg.close()
+    return t_pw + cycles_per_solve * t_cyc, t_pw, t_cyc, O.threads()
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1904_03808_gb300 as Q
+    from paper_1904_03808_gb300 import MG_FP64, MG_MIXED, Context, binding, make_state
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    Q.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    w = workload(args.n)
+    v0, s0, c0, t0 = w.initial_state()
+    K = args.steps
+    W = max(args.warmup, 3)
+
+    def mk(prec):
+        return Context(w.nx, w.ny, w.nz, w.h, I_K(), w.mu, bc=w.bc_values(), stz=w.stz,
+                       precision=prec, max_cycles=100, inner_cycles=args.inner, stream=stream)
+
+    vg = torch.from_numpy(v0).to(dev)
+    sg = torch.from_numpy(s0).to(dev)
+    cg = torch.from_numpy(c0).to(dev)
+    state = make_state(vg, sg, cg, t0)
+    ctx = mk(MG_MIXED)
+    for _ in range(W):
+        ctx.step(state, w.dt, TOL)
+    # snapshot for the FP64 comparison and the oracle sample
+    snap = (vg.clone(), sg.clone(), cg.clone(), state.t)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ctx.profile(True)
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = binding.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    cyc = outer = 0
+    worst = 0.0
+    for _ in range(K):
+        st, s = ctx.step(state, w.dt, TOL)
+        cyc += s.cycles
+        outer += s.outer_iters
+        worst = max(worst, s.rel_resid)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = binding.launch_count() - l0
+    clk = clocks.stop()
+    t_step = ev0.elapsed_time(ev1) / 1e3 / K
+    if ws > 1:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt)
+        dist.barrier()
+    sm_ms, sweeps, sm_launches = ctx.profile_read()
+    ctx.profile(False)
+    n_nodes = w.nx * w.ny * (w.nz - 1)
+    t_sweep = sm_ms / 1e3 / max(sweeps, 1)
+    achieved = SMOOTH_BYTES * n_nodes / t_sweep / 1e9
+    peak, peak_kind = peak_hbm()
+    traffic = traffic_per_sweep(n_nodes)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    vh, sh, ch = (torch.from_numpy(a).pin_memory() for a in (v0, s0, c0))
+    vh.copy_(snap[0])
+    sh.copy_(snap[1])
+    ch.copy_(snap[2])
+    te = snap[3]
+    Ke = max(2, min(K, 5))
+    hstate = make_state(vg, sg, cg, te)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        vg.copy_(vh, non_blocking=True)
+        sg.copy_(sh, non_blocking=True)
+        cg.copy_(ch, non_blocking=True)
+        ctx.step(hstate, w.dt, TOL)
+        vh.copy_(vg, non_blocking=True)
+        sh.copy_(sg, non_blocking=True)
+        ch.copy_(cg, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3 / Ke
+    nbytes = (v0.nbytes + s0.nbytes + c0.nbytes)
+    ctx.close()
+
+    # ---- plain FP64 on the same starting state
+    vg.copy_(snap[0])
+    sg.copy_(snap[1])
+    cg.copy_(snap[2])
+    st64 = make_state(vg, sg, cg, snap[3])
+    ctx64 = mk(MG_FP64)
+    K64 = max(1, min(K, 3))
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    cyc64 = 0
+    for _ in range(K64):
+        _, s = ctx64.step(st64, w.dt, TOL)
+        cyc64 += s.cycles
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t64 = f0.elapsed_time(f1) / 1e3 / K64
+
+    # ---- cold solve of a random right-hand side from v = 0 (mixed and FP64)
+    from paper_1904_03808_gb300 import inputs as I
+    bc = torch.from_numpy(I.rhs_field(1, w.nx, w.ny, w.nz)).to(dev)
+    cold = {}
+    for name, c in (("fp64", ctx64), ("mixed", mk(MG_MIXED))):
+        x = torch.zeros_like(bc)
+        x[0, 0], x[0, w.nz] = -1.0, 1.0
+        c.solve(bc, x.clone(), TOL)  # warm-up of the code path
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        _, s = c.solve(bc, x, TOL)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        cold[name] = {"s": a0.elapsed_time(a1) / 1e3, "cycles": s.cycles,
+                      "outer_iters": s.outer_iters, "rel_resid": s.rel_resid}
+        c.close()
+    del bc
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        vs, ss_, cs_ = (a.cpu().numpy() for a in snap[:3])
+        cps = cyc64 / K64
+        val, t_pw, t_cyc, thr = oracle_sample(w, vs, ss_, cs_, snap[3], cps)
+        cpu = {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": "FP64 C oracle at %d^3: pointwise step pieces once (%.2f s) + one V-cycle "
+                         "with residual norm (%.2f s), scaled by %.1f FP64 cycles per solve"
+                         % (w.nx, t_pw, t_cyc, cps)}
+
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": t_step / ws, "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": W, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycles in f64 refinement",
+        "data": "synthetic (seeded fields of the paper's recipes)",
+        "config": config(w, {"precision": "mixed", "inner_cycles": args.inner,
+                             "parallelism": "replicas" if ws > 1 else "single GPU"}),
+        "solve": {"cycles_per_solve": cyc / K, "outer_per_solve": outer / K,
+                  "worst_rel_resid": worst},
+        "fp64": {"value": t64, "unit": UNIT, "steps": K64, "cycles_per_solve": cyc64 / K64,
+                 "speedup_mixed": t64 / t_step},
+        "cold_solve": cold,
+        "roofline": {"bound": "hbm", "kernel": "finest-level FP32 Gauss-Seidel sweep",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes": SMOOTH_BYTES * n_nodes, "sweep_ms": t_sweep * 1e3,
+                     "launches_per_sweep": sm_launches / max(sweeps, 1),
+                     "share_of_step": sm_ms / 1e3 / K / t_step},
+        "cpu_baseline": cpu,
+        "e2e": {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "steps": Ke},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+
+def I_K():
+    from paper_1904_03808_gb300 import inputs as I
+    return I.TABLE1["K"]
+
+
+# ------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on this host's cores, on a bounded
+    sample per step (see oracle_sample); rank 0 only."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle as O
+    O.build()
+    w = workload(args.n)
+    v, sig, chi, t = w.initial_state()
+    # V-cycles per solve for this workload: one full oracle step at 64^3 of the
+    # same recipe (multigrid cycle counts do not grow with the grid)
+    ws_ = workload(64)
+    vs, ss, cs, ts = ws_.initial_state()
+    mg = O.MG(64, 64, 64, ws_.lam, ws_.mu)
+    st, cps, _ = O.qs_step(mg, vs, ss, cs, ws_.h, ws_.dt, ws_.lam, ws_.mu, O.STZ(**ws_.stz),
+                           O.BC(**ws_.bc_values()), ts, tol=TOL, max_cycles=100)
+    mg.close()
+    vals = []
+    for k in range(args.warmup + args.steps):
+        val, t_pw, t_cyc, thr = oracle_sample(w, v, sig, chi, t, cps)
+        if k >= args.warmup:
+            vals.append(val)
+    value = float(np.mean(vals))
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
+        "data": "synthetic (seeded fields of the paper's recipes)",
+        "config": config(w, {"precision": "fp64 (CPU oracle)"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": "per step: pointwise pieces at %d^3 + one V-cycle and residual, "
+                                   "scaled by %d cycles per solve (oracle, 64^3 first step)"
+                                   % (w.nx, cps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

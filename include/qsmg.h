@@ -1,0 +1,238 @@
+/*
+ * qsmg.h -- C ABI of the GB300 (sm_103a) quasi-static projection library.
+ *
+ * The library implements the hot path of Boffi & Rycroft, "Parallel
+ * three-dimensional simulations of quasi-static elastoplastic solids"
+ * (arXiv 1904.03808): one quasi-static projection step (section 3.3) and the
+ * geometric-multigrid solve of its velocity system (section 3.6), on one GPU.
+ *
+ * Grid (section 3.4, section 4): nx * ny * nz cells of spacing h, periodic in
+ * x and y; velocity at cell corners (i, j, k), i < nx, j < ny, 0 <= k <= nz,
+ * with the planes k = 0 and k = nz holding Dirichlet wall velocities; stress
+ * and effective temperature at cell centres.
+ *
+ * Layouts (all FP64, C-contiguous, x fastest, DEVICE memory unless stated):
+ *   velocity / corner fields   (3, nz+1, ny, nx)   components x, y, z
+ *   stress                     (6, nz, ny, nx)     xx, yy, zz, yz, xz, xy
+ *   effective temperature      (nz, ny, nx)
+ *   stencil table              (27, 3, 3)          offset (dz+1)*9+(dy+1)*3+(dx+1)
+ *
+ * The linear system.  Eq. (30), dt div(C : D^{n+1}) = -div(sigma*), is
+ * discretised with the collocated 3-point second derivative (Eq. 32) and the
+ * 4-point mixed derivative of section 3.4, and scaled by -h^2/(mu dt):
+ *     Ahat v = b,   Ahat = -(h^2/(mu dt)) A,   b = (h^2/(mu dt)) div_h sigma*.
+ * Ahat is symmetric positive definite (section 3.3, condition B) and depends
+ * on lambda/mu only.  Unknowns are the interior corners (0 < k < nz); wall
+ * values enter through the couplings to planes 0 and nz.
+ *
+ * Ownership.  The caller owns every array passed in and keeps it alive for
+ * the call; the library owns its level hierarchy and scratch, allocated in
+ * mg_setup and released by mg_free.  All device work is issued on the stream
+ * given to mg_setup; calls return after that stream has finished the work
+ * they issued (the residual norms are read back to the host).
+ *
+ * Errors.  Every call returns an mg_status; nothing throws or traps.  A
+ * failing call leaves a message for mg_last_error() (thread-local).
+ */
+#ifndef QSMG_H
+#define QSMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_ARG = 1,       /* null pointer, bad option value */
+    MG_ERR_SHAPE = 2,     /* grid not supported (see mg_setup) */
+    MG_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    MG_ERR_OOM = 4,       /* device allocation failed */
+    MG_ERR_NOCONV = 5,    /* max_cycles reached above the tolerance */
+    MG_ERR_NONFINITE = 6, /* residual norm became NaN or Inf */
+    MG_ERR_STATE = 7      /* context unusable (earlier CUDA failure) */
+} mg_status;
+
+enum { MG_FP64 = 0, MG_MIXED = 1 };
+enum { MG_HIST = 128 };
+
+/* Grid: nx, ny even and >= 4, nz even and >= 2 (cells); h spacing (m). */
+typedef struct { int nx, ny, nz; double h; } mg_grid;
+
+/* Isotropic moduli (Pa): bulk K and shear mu; lambda = K - 2 mu / 3
+ * (Table 1 gives K and mu). */
+typedef struct { double K, mu; } mg_moduli;
+
+/*
+ * Wall velocities (section 4, Eqs. 37-38; section 5, Eqs. 48-49).
+ * kind 0 simple shear: v(k=nz) = (+U(t),0,0), v(k=0) = (-U(t),0,0),
+ *   U(t) = U_B t / t_ramp for t < t_ramp, else U_B.
+ * kind 1..3 spinning disc on the top wall, read as a rotation with angular
+ *   velocity omega (rad/s): u = -omega y f, v = omega x f, w = 0 with
+ *   f = 1 for r^2 < R^2, else exp(-lambda_w (r^2 - R^2)^2), r^2 = (x^2+y^2)/L^2,
+ *   L = nx h / 2, x = -L + i h, y = -ny h / 2 + j h.  Bottom wall: kind 1
+ *   fixed, kind 2 the same rotation, kind 3 the opposite rotation.
+ */
+typedef struct {
+    int kind;
+    double U_B, t_ramp, omega, R, lambda_w;
+} mg_bc;
+
+/* STZ plasticity (section 3.1, Table 1).  Energies as temperatures:
+ * Delta_K = Delta/k_B, ez_K = e_z/k_B.  Omega (m^3), kB (J/K), l the chi
+ * diffusion length (m), sY (Pa), tau0 (s). */
+typedef struct {
+    double tau0, eps0, c0, Delta_K, Omega, T, chi_inf, ez_K, sY, l, kB;
+} stz_params;
+
+/*
+ * Solver options.
+ *   precision     MG_FP64: FP64 V-cycles.  MG_MIXED: FP32 V-cycles inside an
+ *                 FP64 iterative-refinement loop (FP64 outer residual, FP64
+ *                 coarsest solve).
+ *   nu1, nu2      pre/post Gauss-Seidel sweeps (section 3.6 uses 2 and 2).
+ *   max_cycles    cap on V-cycles per solve (<= MG_HIST - 1).
+ *   inner_cycles  MG_MIXED: FP32 V-cycles per outer refinement step.
+ */
+typedef struct {
+    int precision;
+    int nu1, nu2;
+    int max_cycles;
+    int inner_cycles;
+} mg_opts;
+
+/* Per-solve statistics.  resid_hist[0] is the relative residual of the
+ * initial guess, resid_hist[c] after V-cycle c (FP64 mode) or after outer
+ * step c (mixed mode).  bnorm is ||b_lifted||_2. */
+typedef struct {
+    int cycles;       /* V-cycles run (FP64 or FP32) */
+    int outer_iters;  /* refinement steps (mixed) or cycles (FP64) */
+    double rel_resid; /* final ||b - Ahat v||_2 / ||b_lifted||_2 */
+    double bnorm;
+    double resid_hist[MG_HIST];
+} mg_stats;
+
+/* Simulation state, caller-owned device arrays (layouts above); t is the
+ * time of the state, step a counter the library increments. */
+typedef struct {
+    double *v, *sigma, *chi;
+    double t;
+    long step;
+} qs_state;
+
+typedef struct mg_ctx mg_ctx;
+
+/*
+ * mg_setup -- build the multigrid hierarchy of section 3.6 for the scaled
+ * operator and allocate every buffer the solve and the step need.
+ *   Levels halve each dimension while all three are even and their halves are
+ *   >= 4 (the paper's ceil(n/2) coarsening restricted to even sizes); coarse
+ *   operators are the Galerkin products A_k = R A_{k-1} T (Eq. 36) with linear
+ *   interpolation T and R = T^T; the coarsest operator is inverted densely
+ *   (at most 3072 unknowns, else MG_ERR_SHAPE).
+ *   stz and bc may be NULL if only mg_solve will be used.
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: MG_ERR_ARG, MG_ERR_SHAPE, MG_ERR_OOM, MG_ERR_CUDA.
+ */
+mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc,
+                   const stz_params *stz, const mg_opts *opts, void *stream, mg_ctx **out);
+
+/*
+ * mg_solve -- multigrid solve of Ahat v = rhs (section 3.6) to
+ *   ||rhs - Ahat v||_2 <= tol * ||b_lifted||_2, where b_lifted is rhs minus the
+ *   wall columns applied to the wall values.  V-cycle: nu1 pre-sweeps of
+ *   8-colour block Gauss-Seidel (colours (i&1)+2(j&1)+4(k&1) visited 0..7),
+ *   residual, restriction, recursive coarse correction, prolongation, nu2
+ *   post-sweeps (colours 7..0); dense solve on the coarsest level.
+ *   rhs: device (3, nz+1, ny, nx); its wall planes are ignored.
+ *   v: device (3, nz+1, ny, nx); in: initial guess (interior) and wall values;
+ *      out: solution (walls unchanged).
+ *   tol <= 0 runs exactly opts.max_cycles V-cycles (or refinement steps) and
+ *   returns MG_OK.  If b_lifted = 0 the interior of v is set to 0.
+ *   stats may be NULL.
+ * Errors: MG_ERR_NOCONV (v holds the last iterate), MG_ERR_NONFINITE,
+ *   MG_ERR_ARG, MG_ERR_CUDA.
+ */
+mg_status mg_solve(mg_ctx *ctx, const double *rhs, double *v, double tol, mg_stats *stats);
+
+/*
+ * qs_step -- one quasi-static projection step (section 3.3) from state->t to
+ * state->t + dt, in place:
+ *   sigma* and D^pl from (v^n, sigma^n, chi^n): Eq. (27) with the STZ rate of
+ *     Eqs. (20)-(22) (D^pl = 0 for sbar <= s_Y) and the Eq. (31) gradient;
+ *   chi^{n+1} by Eq. (26) (conservative diffusion with face-averaged D^pl;
+ *     z ghost cells from linearly extrapolated sigma and chi);
+ *   wall velocities at t + dt; b = (h^2/(mu dt)) div sigma* at interior
+ *   corners; v^{n+1} by mg_solve warm-started from v^n;
+ *   sigma^{n+1} = sigma* + dt C : D^{n+1} (Eq. 29).
+ * Requires stz and bc at setup.  Errors as mg_solve; on a solver error the
+ * state is still advanced with the last iterate.
+ */
+mg_status qs_step(mg_ctx *ctx, qs_state *state, double dt, double tol, mg_stats *stats);
+
+/* Release every buffer of the context (NULL is a no-op). */
+void mg_free(mg_ctx *ctx);
+
+const char *mg_status_str(mg_status s);
+const char *mg_last_error(void);
+
+/* ------------------------------------------------------------------ */
+/* Component entry points (the same kernels the solve and step use),   */
+/* exposed for parity tests against the oracle.  Device pointers, FP64.  */
+/* ------------------------------------------------------------------ */
+
+/* number of levels, and the cell dimensions of one level (dims[3]) */
+int mg_num_levels(const mg_ctx *ctx);
+mg_status mg_level_dims(const mg_ctx *ctx, int level, int *dims);
+
+/* host copy of a level's stencil table (27, 3, 3), scaled operator Ahat */
+mg_status mg_level_stencil(const mg_ctx *ctx, int level, double *host_S);
+
+/* r = b - A_level x on interior nodes, zero on wall planes.  x, b, r are
+ * level-sized corner arrays (3, nz_l+1, ny_l, nx_l); r must not alias x. */
+mg_status mg_residual(mg_ctx *ctx, int level, const double *b, const double *x, double *r);
+
+/* nsweeps Gauss-Seidel sweeps on level `level`, colours 0..7 if
+ * descending == 0 else 7..0; FP64 (precision 0) or FP32 arrays (precision 1). */
+mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps, int descending,
+                    int precision);
+
+/* bc = T^T r (level -> level+1) and x += T xc (level+1 -> level), FP64 */
+mg_status mg_restrict(mg_ctx *ctx, int level, const double *r, double *bc);
+mg_status mg_prolong_add(mg_ctx *ctx, int level, const double *xc, double *x);
+
+/* one FP64 V-cycle on the finest level (b, x as in mg_solve) */
+mg_status mg_vcycle(mg_ctx *ctx, const double *b, double *x);
+
+/* pointwise pieces of qs_step (device arrays; sigma_star 6 per cell, dpl and
+ * sbar 1 per cell, b corner-sized) */
+mg_status qs_stress_predict(mg_ctx *ctx, const double *v, const double *sigma, const double *chi,
+                            double dt, double *sigma_star, double *dpl, double *sbar);
+mg_status qs_chi_update(mg_ctx *ctx, const double *sigma, const double *chi, const double *dpl,
+                        const double *sbar, double dt, double *chi_new);
+mg_status qs_rhs(mg_ctx *ctx, const double *sigma_star, double dt, double *b);
+mg_status qs_stress_correct(mg_ctx *ctx, const double *v, const double *sigma_star, double dt,
+                            double *sigma);
+mg_status qs_wall_fill(mg_ctx *ctx, double *v, double t);
+
+/* ------------------------------------------------------------------ */
+/* Measurement hooks                                                   */
+/* ------------------------------------------------------------------ */
+
+/* Enable (1) or disable (0) timing of the finest-level smoothing calls: a
+ * CUDA event pair is recorded on the context's stream around every pre- and
+ * post-smoothing call on level 0; enabling resets the totals. */
+mg_status mg_profile(mg_ctx *ctx, int enable);
+
+/* Totals since mg_profile(ctx, 1): device milliseconds spent in finest-level
+ * smoothing, sweeps run there, and kernel launches those sweeps made. */
+mg_status mg_profile_read(mg_ctx *ctx, double *smooth_ms, long *smooth_sweeps,
+                          long *smooth_launches);
+
+/* Kernels this library has launched since it was loaded (all contexts). */
+long mg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSMG_H */

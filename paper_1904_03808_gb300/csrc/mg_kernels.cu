@@ -1,0 +1,546 @@
+// mg_kernels.cu -- multigrid kernels for the scaled projection operator
+// (Eq. 30 discretised with the stencils of section 3.4; V-cycle of section 3.6).
+//
+// Layout: corner arrays (3, nz+1, ny, nx), x fastest; planes 0 and nz hold the
+// Dirichlet walls (zero on coarse levels); x and y wrap periodically.
+// Colour of node (i, j, k): (i&1) + 2(j&1) + 4(k&1); a colour pass updates all
+// nodes of one colour at once (no two of them are coupled: every stencil
+// offset lies in {-1,0,1}^3 and the sizes are even).
+#include "qsmg_impl.h"
+
+namespace qsmg {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned nblocks(long n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// finest-level operator (structured 19-point stencil)
+// ---------------------------------------------------------------------------
+
+// value of x at plane kk; with WO ("walls only") interior planes read as zero
+template <typename T, bool WO>
+__device__ __forceinline__ T ldx(const T *x, long idx, int kk, int nz) {
+    if (WO && kk > 0 && kk < nz) return T(0);
+    return x[idx];
+}
+
+// o_a = sum over the 18 non-centre offsets of S_d[a][b] x_b(p + d)
+//   = -( lp x_a(+-e_a) + x_a(+-e_b, b != a) + kq sum_{b!=a} M_ab[x_b] ),
+// M_ab[g] = g(+a,+b) - g(+a,-b) - g(-a,+b) + g(-a,-b)  (4-point mixed difference)
+template <typename T, bool WO>
+__device__ __forceinline__ void fine_off(const T *x, const Dims &d, int i, int j, int k, T lp, T kq,
+                                         T o[3]) {
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const long ps = (long)nx * ny;
+    const int im = i ? i - 1 : nx - 1, ip = (i + 1 < nx) ? i + 1 : 0;
+    const int jm = j ? j - 1 : ny - 1, jp = (j + 1 < ny) ? j + 1 : 0;
+    const long pc = (long)k * ps, pm = pc - ps, pp = pc + ps;
+    const long r0 = (long)j * nx, rm = (long)jm * nx, rp = (long)jp * nx;
+    const T *x0 = x, *x1 = x + d.cs, *x2 = x + 2 * d.cs;
+#define XC(g, r, c) ldx<T, WO>(g, pc + (r) + (c), k, nz)
+#define XM(g, r, c) ldx<T, WO>(g, pm + (r) + (c), k - 1, nz)
+#define XP(g, r, c) ldx<T, WO>(g, pp + (r) + (c), k + 1, nz)
+    const T a0 = lp * (XC(x0, r0, im) + XC(x0, r0, ip)) + (XC(x0, rm, i) + XC(x0, rp, i)) +
+                 (XM(x0, r0, i) + XP(x0, r0, i));
+    const T a1 = lp * (XC(x1, rm, i) + XC(x1, rp, i)) + (XC(x1, r0, im) + XC(x1, r0, ip)) +
+                 (XM(x1, r0, i) + XP(x1, r0, i));
+    const T a2 = lp * (XM(x2, r0, i) + XP(x2, r0, i)) + (XC(x2, r0, im) + XC(x2, r0, ip)) +
+                 (XC(x2, rm, i) + XC(x2, rp, i));
+#define MXY(g) (XC(g, rp, ip) - XC(g, rm, ip) - XC(g, rp, im) + XC(g, rm, im))
+#define MXZ(g) (XP(g, r0, ip) - XM(g, r0, ip) - XP(g, r0, im) + XM(g, r0, im))
+#define MYZ(g) (XP(g, rp, i) - XM(g, rp, i) - XP(g, rm, i) + XM(g, rm, i))
+    o[0] = -(a0 + kq * (MXY(x1) + MXZ(x2)));
+    o[1] = -(a1 + kq * (MXY(x0) + MYZ(x2)));
+    o[2] = -(a2 + kq * (MXZ(x0) + MYZ(x1)));
+#undef XC
+#undef XM
+#undef XP
+#undef MXY
+#undef MXZ
+#undef MYZ
+}
+
+// general 27-point block stencil, off-centre part
+template <typename T>
+__device__ __forceinline__ void coarse_off(const T *x, const Dims &d, int i, int j, int k,
+                                           const Coarse<T> &c, T o[3]) {
+    const int nx = d.nx, ny = d.ny;
+    T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz++) {
+        const long pl = (long)(k + dz) * ny;
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++) {
+            int jj = j + dy;
+            jj = jj < 0 ? jj + ny : (jj >= ny ? jj - ny : jj);
+            const long row = (pl + jj) * nx;
+#pragma unroll
+            for (int dx = -1; dx <= 1; dx++) {
+                const int dd = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                if (dd == 13) continue;
+                int ii = i + dx;
+                ii = ii < 0 ? ii + nx : (ii >= nx ? ii - nx : ii);
+                const long q = row + ii;
+                const T v0 = x[q], v1 = x[q + d.cs], v2 = x[q + 2 * d.cs];
+                const T *s = c.S + dd * 9;
+                s0 += s[0] * v0 + s[1] * v1 + s[2] * v2;
+                s1 += s[3] * v0 + s[4] * v1 + s[5] * v2;
+                s2 += s[6] * v0 + s[7] * v1 + s[8] * v2;
+            }
+        }
+    }
+    o[0] = s0;
+    o[1] = s1;
+    o[2] = s2;
+}
+
+// node of colour `colour` number t (t < (nx/2)(ny/2)nk)
+__device__ __forceinline__ void colour_node(long t, int colour, int hx, int hy, int &i, int &j,
+                                            int &k) {
+    const int ix = (int)(t % hx);
+    const long q = t / hx;
+    const int jy = (int)(q % hy);
+    const int kz = (int)(q / hy);
+    i = 2 * ix + (colour & 1);
+    j = 2 * jy + ((colour >> 1) & 1);
+    k = 2 * kz + ((colour & 4) ? 1 : 2);
+}
+
+// planes of one k-parity among the interior planes 1..nz-1
+inline int colour_planes(int nz, int colour) { return (colour & 4) ? nz / 2 : nz / 2 - 1; }
+
+template <typename T>
+__global__ void k_gs_fine(Dims d, Fine<T> f, const T *__restrict__ b, T *x, int colour, int hx,
+                          int hy, long tot) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    int i, j, k;
+    colour_node(t, colour, hx, hy, i, j, k);
+    T o[3];
+    fine_off<T, false>(x, d, i, j, k, f.lp, f.kq, o);
+    const long p = ((long)k * d.ny + j) * d.nx + i;
+    const T u0 = (b[p] - o[0]) * f.dinv;
+    const T u1 = (b[p + d.cs] - o[1]) * f.dinv;
+    const T u2 = (b[p + 2 * d.cs] - o[2]) * f.dinv;
+    x[p] = u0;
+    x[p + d.cs] = u1;
+    x[p + 2 * d.cs] = u2;
+}
+
+template <typename T>
+__global__ void k_gs_coarse(Dims d, Coarse<T> c, const T *__restrict__ b, T *x, int colour, int hx,
+                            int hy, long tot) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    int i, j, k;
+    colour_node(t, colour, hx, hy, i, j, k);
+    T o[3];
+    coarse_off<T>(x, d, i, j, k, c, o);
+    const long p = ((long)k * d.ny + j) * d.nx + i;
+    const T f0 = b[p] - o[0], f1 = b[p + d.cs] - o[1], f2 = b[p + 2 * d.cs] - o[2];
+    x[p] = c.Dinv[0] * f0 + c.Dinv[1] * f1 + c.Dinv[2] * f2;
+    x[p + d.cs] = c.Dinv[3] * f0 + c.Dinv[4] * f1 + c.Dinv[5] * f2;
+    x[p + 2 * d.cs] = c.Dinv[6] * f0 + c.Dinv[7] * f1 + c.Dinv[8] * f2;
+}
+
+// interior node number t -> (i, j, k), k in 1..nz-1
+__device__ __forceinline__ void interior_node(long t, const Dims &d, int &i, int &j, int &k) {
+    i = (int)(t % d.nx);
+    const long q = t / d.nx;
+    j = (int)(q % d.ny);
+    k = (int)(q / d.ny) + 1;
+}
+
+template <typename T>
+__global__ void k_res_fine(Dims d, Fine<T> f, const T *__restrict__ b, const T *__restrict__ x,
+                           T *__restrict__ r, long tot) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    int i, j, k;
+    interior_node(t, d, i, j, k);
+    T o[3];
+    fine_off<T, false>(x, d, i, j, k, f.lp, f.kq, o);
+    const long p = ((long)k * d.ny + j) * d.nx + i;
+#pragma unroll
+    for (int a = 0; a < 3; a++) r[p + a * d.cs] = b[p + a * d.cs] - (f.d0 * x[p + a * d.cs] + o[a]);
+}
+
+template <typename T>
+__global__ void k_res_coarse(Dims d, Coarse<T> c, const T *__restrict__ b,
+                             const T *__restrict__ x, T *__restrict__ r, long tot) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    int i, j, k;
+    interior_node(t, d, i, j, k);
+    T o[3];
+    coarse_off<T>(x, d, i, j, k, c, o);
+    const long p = ((long)k * d.ny + j) * d.nx + i;
+    const T x0 = x[p], x1 = x[p + d.cs], x2 = x[p + 2 * d.cs];
+    const T *s = c.S + 13 * 9;
+    r[p] = b[p] - (o[0] + s[0] * x0 + s[1] * x1 + s[2] * x2);
+    r[p + d.cs] = b[p + d.cs] - (o[1] + s[3] * x0 + s[4] * x1 + s[5] * x2);
+    r[p + 2 * d.cs] = b[p + 2 * d.cs] - (o[2] + s[6] * x0 + s[7] * x1 + s[8] * x2);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// fixed-order block sum; result valid in thread 0
+__device__ double block_sum(double v) {
+    __shared__ double sh[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    return v;
+}
+
+template <bool WO>
+__global__ void __launch_bounds__(kRedThreads)
+    k_res_norm_fine64(Dims d, Fine<double> f, const double *__restrict__ b,
+                      const double *__restrict__ x, float *__restrict__ r32, double out_scale,
+                      double *__restrict__ partials, long tot) {
+    double acc = 0.0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += stride) {
+        int i, j, k;
+        interior_node(t, d, i, j, k);
+        double o[3];
+        fine_off<double, WO>(x, d, i, j, k, f.lp, f.kq, o);
+        const long p = ((long)k * d.ny + j) * d.nx + i;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double xc = WO ? 0.0 : x[p + a * d.cs];
+            const double r = b[p + a * d.cs] - (f.d0 * xc + o[a]);
+            acc += r * r;
+            if (r32) r32[p + a * d.cs] = (float)(r * out_scale);
+        }
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_sumsq(Dims d, const double *__restrict__ r, double *__restrict__ partials, long tot) {
+    double acc = 0.0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    const long plane0 = (long)d.ny * d.nx;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += stride) {
+        const long p = t + plane0;  // interior nodes of component 0 are contiguous
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double v = r[p + a * d.cs];
+            acc += v * v;
+        }
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_sum_partials(const double *__restrict__ partials,
+                                                        double *__restrict__ out) {
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < kRedBlocks; t += 1024) acc += partials[t];
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) out[0] = s;
+}
+
+// restriction R = T^T (full weighting, weights 1, 1/2, 1/4, 1/8 by the
+// number of odd offsets), coarse interior nodes
+template <typename T>
+__global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restrict__ bc, long tot) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    int I, J, K;
+    interior_node(t, c, I, J, K);
+    T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int ez = -1; ez <= 1; ez++) {
+        const T wz = ez ? T(0.5) : T(1);
+        const long pl = (long)(2 * K + ez) * f.ny;
+#pragma unroll
+        for (int ey = -1; ey <= 1; ey++) {
+            const T wy = ey ? T(0.5) : T(1);
+            int jj = 2 * J + ey;
+            jj = jj < 0 ? jj + f.ny : (jj >= f.ny ? jj - f.ny : jj);
+            const long row = (pl + jj) * f.nx;
+#pragma unroll
+            for (int ex = -1; ex <= 1; ex++) {
+                const T w = (ex ? T(0.5) : T(1)) * wy * wz;
+                int ii = 2 * I + ex;
+                ii = ii < 0 ? ii + f.nx : (ii >= f.nx ? ii - f.nx : ii);
+                const long q = row + ii;
+                s0 += w * r[q];
+                s1 += w * r[q + f.cs];
+                s2 += w * r[q + 2 * f.cs];
+            }
+        }
+    }
+    const long p = ((long)K * c.ny + J) * c.nx + I;
+    bc[p] = s0;
+    bc[p + c.cs] = s1;
+    bc[p + 2 * c.cs] = s2;
+}
+
+// prolongation x += T xc: fine node 2I is coarse node I, odd fine nodes take
+// the mean of their two neighbours along each odd axis (coarse walls are 0)
+template <typename T>
+__global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restrict__ x, long tot) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    int i, j, k;
+    interior_node(t, f, i, j, k);
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int I1 = (i & 1) ? ((I0 + 1 < c.nx) ? I0 + 1 : 0) : I0;
+    const int J1 = (j & 1) ? ((J0 + 1 < c.ny) ? J0 + 1 : 0) : J0;
+    const int K1 = (k & 1) ? K0 + 1 : K0;
+    const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1), wz = (k & 1) ? T(0.5) : T(1);
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+    const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
+    const long p = ((long)k * f.ny + j) * f.nx + i;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        T s = 0;
+        for (int u = 0; u < nk; u++)
+            for (int v = 0; v < nj; v++)
+                for (int w = 0; w < ni; w++)
+                    s += xc[a * c.cs + ((long)Ks[u] * c.ny + Js[v]) * c.nx + Is[w]];
+        x[p + a * f.cs] += wx * wy * wz * s;
+    }
+}
+
+// x += Ainv r on the coarsest level; one warp per unknown, fixed-order sums.
+// unknown u = (((k-1) ny + j) nx + i) * 3 + a
+template <typename T>
+__global__ void k_coarse_solve(Dims d, const double *__restrict__ Ainv, int n,
+                               const T *__restrict__ r, T *__restrict__ x) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    double acc = 0.0;
+    const long plane0 = (long)d.ny * d.nx;
+    for (int v = lane; v < n; v += 32) {
+        const int a = v % 3;
+        const long node = v / 3;  // ((k-1) ny + j) nx + i
+        acc += Ainv[(long)warp * n + v] * (double)r[a * d.cs + plane0 + node];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        const int a = warp % 3;
+        const long node = warp / 3;
+        const long p = a * d.cs + plane0 + node;
+        x[p] = (T)((double)x[p] + acc);
+    }
+}
+
+__global__ void k_zero_interior(Dims d, double *__restrict__ x, long tot) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    const long plane0 = (long)d.ny * d.nx;
+#pragma unroll
+    for (int a = 0; a < 3; a++) x[a * d.cs + plane0 + t] = 0.0;
+}
+
+__global__ void k_axpy_f32(Dims d, double scale, const float *__restrict__ e,
+                           double *__restrict__ v, long tot) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    const long p = (long)d.ny * d.nx + t;
+#pragma unroll
+    for (int a = 0; a < 3; a++) v[a * d.cs + p] += scale * (double)e[a * d.cs + p];
+}
+
+inline long interior_nodes(const Dims &d) { return (long)d.nx * d.ny * (d.nz - 1); }
+
+template <typename T>
+cudaError_t gs_fine_t(const Dims &d, const Fine<T> &f, const T *b, T *x, int colour,
+                      cudaStream_t s) {
+    const int hx = d.nx / 2, hy = d.ny / 2, nk = colour_planes(d.nz, colour);
+    const long tot = (long)hx * hy * nk;
+    if (tot <= 0) return cudaSuccess;
+    k_gs_fine<T><<<nblocks(tot), kThreads, 0, s>>>(d, f, b, x, colour, hx, hy, tot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gs_coarse_t(const Dims &d, const Coarse<T> &c, const T *b, T *x, int colour,
+                        cudaStream_t s) {
+    const int hx = d.nx / 2, hy = d.ny / 2, nk = colour_planes(d.nz, colour);
+    const long tot = (long)hx * hy * nk;
+    if (tot <= 0) return cudaSuccess;
+    k_gs_coarse<T><<<nblocks(tot), kThreads, 0, s>>>(d, c, b, x, colour, hx, hy, tot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t gs_colour_fine(const Dims &d, const Fine<double> &f, const double *b, double *x,
+                           int colour, cudaStream_t s) {
+    return gs_fine_t(d, f, b, x, colour, s);
+}
+cudaError_t gs_colour_fine(const Dims &d, const Fine<float> &f, const float *b, float *x,
+                           int colour, cudaStream_t s) {
+    return gs_fine_t(d, f, b, x, colour, s);
+}
+cudaError_t gs_colour_coarse(const Dims &d, const Coarse<double> &c, const double *b, double *x,
+                             int colour, cudaStream_t s) {
+    return gs_coarse_t(d, c, b, x, colour, s);
+}
+cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float *b, float *x,
+                             int colour, cudaStream_t s) {
+    return gs_coarse_t(d, c, b, x, colour, s);
+}
+
+template <typename T>
+static cudaError_t res_fine_t(const Dims &d, const Fine<T> &f, const T *b, const T *x, T *r,
+                              cudaStream_t s) {
+    const long tot = interior_nodes(d);
+    k_res_fine<T><<<nblocks(tot), kThreads, 0, s>>>(d, f, b, x, r, tot);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // wall planes of r are zero
+    const long plane = (long)d.ny * d.nx;
+    for (int a = 0; a < 3; a++) {
+        e = cudaMemsetAsync(r + a * d.cs, 0, plane * sizeof(T), s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(r + a * d.cs + (long)d.nz * plane, 0, plane * sizeof(T), s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t res_coarse_t(const Dims &d, const Coarse<T> &c, const T *b, const T *x, T *r,
+                                cudaStream_t s) {
+    const long tot = interior_nodes(d);
+    k_res_coarse<T><<<nblocks(tot), kThreads, 0, s>>>(d, c, b, x, r, tot);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long plane = (long)d.ny * d.nx;
+    for (int a = 0; a < 3; a++) {
+        e = cudaMemsetAsync(r + a * d.cs, 0, plane * sizeof(T), s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(r + a * d.cs + (long)d.nz * plane, 0, plane * sizeof(T), s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t residual_fine(const Dims &d, const Fine<double> &f, const double *b, const double *x,
+                          double *r, cudaStream_t s) {
+    return res_fine_t(d, f, b, x, r, s);
+}
+cudaError_t residual_fine(const Dims &d, const Fine<float> &f, const float *b, const float *x,
+                          float *r, cudaStream_t s) {
+    return res_fine_t(d, f, b, x, r, s);
+}
+cudaError_t residual_coarse(const Dims &d, const Coarse<double> &c, const double *b,
+                            const double *x, double *r, cudaStream_t s) {
+    return res_coarse_t(d, c, b, x, r, s);
+}
+cudaError_t residual_coarse(const Dims &d, const Coarse<float> &c, const float *b, const float *x,
+                            float *r, cudaStream_t s) {
+    return res_coarse_t(d, c, b, x, r, s);
+}
+
+cudaError_t residual_norm_fine64(const Dims &d, const Fine<double> &f, const double *b,
+                                 const double *x, bool wall_only, float *r32, double out_scale,
+                                 double *partials, cudaStream_t s) {
+    const long tot = interior_nodes(d);
+    if (wall_only)
+        k_res_norm_fine64<true><<<kRedBlocks, kRedThreads, 0, s>>>(d, f, b, x, r32, out_scale,
+                                                                   partials, tot);
+    else
+        k_res_norm_fine64<false><<<kRedBlocks, kRedThreads, 0, s>>>(d, f, b, x, r32, out_scale,
+                                                                    partials, tot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t sumsq(const Dims &d, const double *r, double *partials, cudaStream_t s) {
+    k_sumsq<<<kRedBlocks, kRedThreads, 0, s>>>(d, r, partials, interior_nodes(d));
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t sum_partials(const double *partials, double *out, cudaStream_t s) {
+    k_sum_partials<<<1, 1024, 0, s>>>(partials, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t restrict_t(const Dims &f, const T *r, T *bc, cudaStream_t s) {
+    const Dims c = make_dims(f.nx / 2, f.ny / 2, f.nz / 2);
+    const long tot = interior_nodes(c);
+    if (tot > 0) k_restrict<T><<<nblocks(tot), kThreads, 0, s>>>(f, c, r, bc, tot);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t restrict_fw(const Dims &fine, const double *r, double *bc, cudaStream_t s) {
+    return restrict_t(fine, r, bc, s);
+}
+cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_t s) {
+    return restrict_t(fine, r, bc, s);
+}
+
+template <typename T>
+static cudaError_t prolong_t(const Dims &f, const T *xc, T *x, cudaStream_t s) {
+    const Dims c = make_dims(f.nx / 2, f.ny / 2, f.nz / 2);
+    const long tot = interior_nodes(f);
+    k_prolong<T><<<nblocks(tot), kThreads, 0, s>>>(f, c, xc, x, tot);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t prolong_add(const Dims &fine, const double *xc, double *x, cudaStream_t s) {
+    return prolong_t(fine, xc, x, s);
+}
+cudaError_t prolong_add(const Dims &fine, const float *xc, float *x, cudaStream_t s) {
+    return prolong_t(fine, xc, x, s);
+}
+
+template <typename T>
+static cudaError_t coarse_t(const Dims &d, const double *Ainv, int n, const T *r, T *x,
+                            cudaStream_t s) {
+    const long threads = (long)n * 32;
+    k_coarse_solve<T><<<nblocks(threads), kThreads, 0, s>>>(d, Ainv, n, r, x);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t coarse_solve(const Dims &d, const double *Ainv, int n, const double *r, double *x,
+                         cudaStream_t s) {
+    return coarse_t(d, Ainv, n, r, x, s);
+}
+cudaError_t coarse_solve(const Dims &d, const double *Ainv, int n, const float *r, float *x,
+                         cudaStream_t s) {
+    return coarse_t(d, Ainv, n, r, x, s);
+}
+
+cudaError_t zero_interior(const Dims &d, double *x, cudaStream_t s) {
+    const long tot = interior_nodes(d);
+    k_zero_interior<<<nblocks(tot), kThreads, 0, s>>>(d, x, tot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t axpy_f32(const Dims &d, double scale, const float *e, double *v, cudaStream_t s) {
+    const long tot = interior_nodes(d);
+    k_axpy_f32<<<nblocks(tot), kThreads, 0, s>>>(d, scale, e, v, tot);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace qsmg

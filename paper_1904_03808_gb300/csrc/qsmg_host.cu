@@ -1,0 +1,896 @@
+// qsmg_host.cu -- host side of the C ABI declared in include/qsmg.h:
+// hierarchy set-up (Galerkin coarse operators, dense coarsest inverse),
+// V-cycle and solve orchestration (FP64, and FP32 cycles inside FP64
+// iterative refinement), the projection step, and the component entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/qsmg.h"
+#include "qsmg_impl.h"
+
+using namespace qsmg;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+constexpr int kMaxLev = 16;
+constexpr int kMaxCoarse = 3072;
+constexpr int kProfSlots = 64;
+
+}  // namespace
+
+std::atomic<long> qsmg::g_launches{0};
+
+struct mg_ctx {
+    int nlev;
+    Dims L[kMaxLev];
+    double S[kMaxLev][243];  // host stencil tables of the scaled operator
+    Fine<double> f64;
+    Fine<float> f32;
+    Coarse<double> c64[kMaxLev];
+    Coarse<float> c32[kMaxLev];
+    double lam, mu, h;
+    mg_bc bc;
+    stz_params stz;
+    bool has_bc, has_stz;
+    mg_opts opts;
+    cudaStream_t st;
+    bool broken;
+    // device buffers (level 0 x/b in FP64 mode are the caller's arrays)
+    double *x64[kMaxLev], *b64[kMaxLev], *r64[kMaxLev];
+    float *x32[kMaxLev], *b32[kMaxLev], *r32[kMaxLev];
+    double *Ainv;
+    int ncoarse;
+    double *partials, *dsum, *hsum;
+    double *sig_star, *dpl, *sbar, *chi_tmp, *rhs;
+    // finest-level smoothing timers (event pairs recorded on st)
+    bool prof_on, prof_events;
+    cudaEvent_t ev[kProfSlots][2];
+    long pend_sweeps[kProfSlots], pend_launches[kProfSlots];
+    int npend;
+    double prof_ms;
+    long prof_sweeps, prof_launches;
+    std::vector<void *> allocs;
+};
+
+#define CK(expr)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_err("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                    __LINE__);                                                          \
+            if (ctx) ctx->broken = true;                                                \
+            return MG_ERR_CUDA;                                                         \
+        }                                                                               \
+    } while (0)
+
+#define CKS(expr)                         \
+    do {                                  \
+        mg_status s_ = (expr);            \
+        if (s_ != MG_OK) return s_;       \
+    } while (0)
+
+namespace {
+
+// ---------------------------------------------------------------- set-up
+
+// Scaled finest-level stencil (27, 3, 3): Eq. (30) with the collocated
+// 3-point second derivative (Eq. 32) and 4-point mixed derivative of
+// section 3.4, multiplied by -h^2/(mu dt).
+void fine_table(double lam, double mu, double *S) {
+    const double lp = (lam + 2.0 * mu) / mu, kq = (lam + mu) / (4.0 * mu);
+    memset(S, 0, 243 * sizeof(double));
+    auto at = [&](int dx, int dy, int dz, int a, int b) -> double & {
+        return S[((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) * 9 + a * 3 + b];
+    };
+    for (int a = 0; a < 3; a++) at(0, 0, 0, a, a) = 2.0 * lp + 4.0;
+    for (int ax = 0; ax < 3; ax++)
+        for (int s = -1; s <= 1; s += 2) {
+            int o[3] = {0, 0, 0};
+            o[ax] = s;
+            for (int a = 0; a < 3; a++) at(o[0], o[1], o[2], a, a) = (a == ax) ? -lp : -1.0;
+        }
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            if (a == b) continue;
+            for (int sa = -1; sa <= 1; sa += 2)
+                for (int sb = -1; sb <= 1; sb += 2) {
+                    int o[3] = {0, 0, 0};
+                    o[a] = sa;
+                    o[b] = sb;
+                    at(o[0], o[1], o[2], a, b) = -kq * sa * sb;
+                }
+        }
+}
+
+// Galerkin coarse stencil A_c = R A T (Eq. 36) in two separable stages:
+//   AT(g)  = sum_f t(f) A(g + f)          g in [-3, 3]^3  (operator times interpolation)
+//   A_c(D) = sum_e t(e) AT(2D - e)        D in [-1, 1]^3  (restriction, stride 2)
+// with the trilinear weights t(e) = prod (1 - |e_axis|/2).
+void galerkin_table(const double *Sf, double *Sc) {
+    static double AT[7][7][7][9];
+    memset(AT, 0, sizeof(AT));
+    auto t1 = [](int e) { return e == 0 ? 1.0 : 0.5; };
+    for (int gz = -3; gz <= 3; gz++)
+        for (int gy = -3; gy <= 3; gy++)
+            for (int gx = -3; gx <= 3; gx++)
+                for (int fz = -1; fz <= 1; fz++)
+                    for (int fy = -1; fy <= 1; fy++)
+                        for (int fx = -1; fx <= 1; fx++) {
+                            const int ax = gx + fx, ay = gy + fy, az = gz + fz;
+                            if (ax < -1 || ax > 1 || ay < -1 || ay > 1 || az < -1 || az > 1)
+                                continue;
+                            const double w = t1(fx) * t1(fy) * t1(fz);
+                            const double *a = Sf + ((az + 1) * 9 + (ay + 1) * 3 + (ax + 1)) * 9;
+                            double *o = AT[gz + 3][gy + 3][gx + 3];
+                            for (int m = 0; m < 9; m++) o[m] += w * a[m];
+                        }
+    memset(Sc, 0, 243 * sizeof(double));
+    for (int Dz = -1; Dz <= 1; Dz++)
+        for (int Dy = -1; Dy <= 1; Dy++)
+            for (int Dx = -1; Dx <= 1; Dx++) {
+                double *o = Sc + ((Dz + 1) * 9 + (Dy + 1) * 3 + (Dx + 1)) * 9;
+                for (int ez = -1; ez <= 1; ez++)
+                    for (int ey = -1; ey <= 1; ey++)
+                        for (int ex = -1; ex <= 1; ex++) {
+                            const double w = t1(ex) * t1(ey) * t1(ez);
+                            const double *a = AT[2 * Dz - ez + 3][2 * Dy - ey + 3][2 * Dx - ex + 3];
+                            for (int m = 0; m < 9; m++) o[m] += w * a[m];
+                        }
+            }
+}
+
+bool invert3(const double *M, double *Mi) {
+    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8],
+                 c02 = M[3] * M[7] - M[4] * M[6];
+    const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+    if (!(fabs(det) > 0.0)) return false;
+    const double id = 1.0 / det;
+    Mi[0] = c00 * id;
+    Mi[1] = (M[2] * M[7] - M[1] * M[8]) * id;
+    Mi[2] = (M[1] * M[5] - M[2] * M[4]) * id;
+    Mi[3] = c01 * id;
+    Mi[4] = (M[0] * M[8] - M[2] * M[6]) * id;
+    Mi[5] = (M[2] * M[3] - M[0] * M[5]) * id;
+    Mi[6] = c02 * id;
+    Mi[7] = (M[1] * M[6] - M[0] * M[7]) * id;
+    Mi[8] = (M[0] * M[4] - M[1] * M[3]) * id;
+    return true;
+}
+
+// dense inverse of the coarsest operator (interior unknowns, ordering
+// u = (((k-1) ny + j) nx + i) * 3 + a) via a Cholesky factorisation
+bool coarse_inverse(const Dims &d, const double *S, std::vector<double> &Ainv) {
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const int n = 3 * nx * ny * (nz - 1);
+    std::vector<double> A((size_t)n * n, 0.0);
+    auto unk = [&](int a, int k, int j, int i) { return (((k - 1) * ny + j) * nx + i) * 3 + a; };
+    for (int k = 1; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++)
+                for (int dd = 0; dd < 27; dd++) {
+                    const int dz = dd / 9 - 1, dy = (dd / 3) % 3 - 1, dx = dd % 3 - 1;
+                    const int kk = k + dz;
+                    if (kk < 1 || kk >= nz) continue;
+                    const int jj = (j + dy + ny) % ny, ii = (i + dx + nx) % nx;
+                    for (int a = 0; a < 3; a++)
+                        for (int b = 0; b < 3; b++)
+                            A[(size_t)unk(a, k, j, i) * n + unk(b, kk, jj, ii)] += S[dd * 9 + a * 3 + b];
+                }
+    // Cholesky A = L L^T (lower part of A overwritten)
+    for (int c = 0; c < n; c++) {
+        double s = A[(size_t)c * n + c];
+        for (int p = 0; p < c; p++) s -= A[(size_t)c * n + p] * A[(size_t)c * n + p];
+        if (!(s > 0.0)) return false;
+        const double l = sqrt(s);
+        A[(size_t)c * n + c] = l;
+        for (int r = c + 1; r < n; r++) {
+            double t = A[(size_t)r * n + c];
+            for (int p = 0; p < c; p++) t -= A[(size_t)r * n + p] * A[(size_t)c * n + p];
+            A[(size_t)r * n + c] = t / l;
+        }
+    }
+    Ainv.assign((size_t)n * n, 0.0);
+    std::vector<double> y(n);
+    for (int col = 0; col < n; col++) {
+        for (int r = 0; r < n; r++) {
+            double s = (r == col) ? 1.0 : 0.0;
+            for (int p = 0; p < r; p++) s -= A[(size_t)r * n + p] * y[p];
+            y[r] = s / A[(size_t)r * n + r];
+        }
+        for (int r = n - 1; r >= 0; r--) {
+            double s = y[r];
+            for (int p = r + 1; p < n; p++) s -= A[(size_t)p * n + r] * y[p];
+            y[r] = s / A[(size_t)r * n + r];
+        }
+        for (int r = 0; r < n; r++) Ainv[(size_t)r * n + col] = y[r];
+    }
+    return true;
+}
+
+template <typename T>
+mg_status dalloc(mg_ctx *ctx, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        set_err("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        cudaGetLastError();
+        return MG_ERR_OOM;
+    }
+    ctx->allocs.push_back(q);
+    e = cudaMemsetAsync(q, 0, count * sizeof(T), ctx->st);
+    if (e != cudaSuccess) {
+        set_err("cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+        return MG_ERR_CUDA;
+    }
+    *p = (T *)q;
+    return MG_OK;
+}
+
+bool can_coarsen(const Dims &d) {
+    const int n[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; a++)
+        if (n[a] % 2 != 0 || n[a] / 2 < 4) return false;
+    return true;
+}
+
+size_t corner_count(const Dims &d) { return 3 * (size_t)d.cs; }
+
+// ---------------------------------------------------------------- timers
+
+// fold completed event pairs into the totals (the stream must be idle)
+mg_status prof_drain(mg_ctx *ctx) {
+    for (int i = 0; i < ctx->npend; i++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]));
+        ctx->prof_ms += ms;
+        ctx->prof_sweeps += ctx->pend_sweeps[i];
+        ctx->prof_launches += ctx->pend_launches[i];
+    }
+    ctx->npend = 0;
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- norms
+
+// ||r||^2 from the partial sums of the last reduction kernel
+mg_status read_sum(mg_ctx *ctx, double *out) {
+    CK(sum_partials(ctx->partials, ctx->dsum, ctx->st));
+    CK(cudaMemcpyAsync(ctx->hsum, ctx->dsum, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *out = ctx->hsum[0];
+    return prof_drain(ctx);
+}
+
+// ||b - A v||_2 on the finest level (FP64), optionally writing
+// float(r * out_scale) into r32; wall_only gives ||b_lifted||_2
+mg_status fine_resnorm(mg_ctx *ctx, const double *b, const double *v, bool wall_only, float *r32,
+                       double out_scale, double *norm) {
+    CK(residual_norm_fine64(ctx->L[0], ctx->f64, b, v, wall_only, r32, out_scale, ctx->partials,
+                            ctx->st));
+    double s2;
+    CKS(read_sum(ctx, &s2));
+    *norm = sqrt(s2);
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- V-cycles
+
+template <typename T>
+struct Bufs;
+template <>
+struct Bufs<double> {
+    static double *x(mg_ctx *c, int l) { return c->x64[l]; }
+    static double *b(mg_ctx *c, int l) { return c->b64[l]; }
+    static double *r(mg_ctx *c, int l) { return c->r64[l]; }
+    static const Fine<double> &fine(mg_ctx *c) { return c->f64; }
+    static const Coarse<double> &coarse(mg_ctx *c, int l) { return c->c64[l]; }
+};
+template <>
+struct Bufs<float> {
+    static float *x(mg_ctx *c, int l) { return c->x32[l]; }
+    static float *b(mg_ctx *c, int l) { return c->b32[l]; }
+    static float *r(mg_ctx *c, int l) { return c->r32[l]; }
+    static const Fine<float> &fine(mg_ctx *c) { return c->f32; }
+    static const Coarse<float> &coarse(mg_ctx *c, int l) { return c->c32[l]; }
+};
+
+template <typename T>
+mg_status gs_pass(mg_ctx *ctx, int l, const T *b, T *x, int colour) {
+    if (l == 0)
+        CK(gs_colour_fine(ctx->L[0], Bufs<T>::fine(ctx), b, x, colour, ctx->st));
+    else
+        CK(gs_colour_coarse(ctx->L[l], Bufs<T>::coarse(ctx, l), b, x, colour, ctx->st));
+    return MG_OK;
+}
+
+template <typename T>
+mg_status smooth(mg_ctx *ctx, int l, const T *b, T *x, int sweeps, bool descending) {
+    const bool timed = ctx->prof_on && l == 0 && sweeps > 0;
+    if (timed && ctx->npend == kProfSlots) {
+        CK(cudaStreamSynchronize(ctx->st));
+        CKS(prof_drain(ctx));
+    }
+    const long launches0 = g_launches.load();
+    if (timed) CK(cudaEventRecord(ctx->ev[ctx->npend][0], ctx->st));
+    for (int s = 0; s < sweeps; s++)
+        for (int c = 0; c < 8; c++) CKS(gs_pass<T>(ctx, l, b, x, descending ? 7 - c : c));
+    if (timed) {
+        CK(cudaEventRecord(ctx->ev[ctx->npend][1], ctx->st));
+        ctx->pend_sweeps[ctx->npend] = sweeps;
+        ctx->pend_launches[ctx->npend] = g_launches.load() - launches0;
+        ctx->npend++;
+    }
+    return MG_OK;
+}
+
+template <typename T>
+mg_status residual_level(mg_ctx *ctx, int l, const T *b, const T *x, T *r) {
+    if (l == 0)
+        CK(residual_fine(ctx->L[0], Bufs<T>::fine(ctx), b, x, r, ctx->st));
+    else
+        CK(residual_coarse(ctx->L[l], Bufs<T>::coarse(ctx, l), b, x, r, ctx->st));
+    return MG_OK;
+}
+
+// one V-cycle for A_l x = b on level l (section 3.6)
+template <typename T>
+mg_status vcycle(mg_ctx *ctx, int l, const T *b, T *x) {
+    T *r = Bufs<T>::r(ctx, l);
+    if (l == ctx->nlev - 1) {
+        CKS(residual_level<T>(ctx, l, b, x, r));
+        CK(coarse_solve(ctx->L[l], ctx->Ainv, ctx->ncoarse, r, x, ctx->st));
+        return MG_OK;
+    }
+    CKS(smooth<T>(ctx, l, b, x, ctx->opts.nu1, false));
+    CKS(residual_level<T>(ctx, l, b, x, r));
+    T *bc = Bufs<T>::b(ctx, l + 1), *xc = Bufs<T>::x(ctx, l + 1);
+    CK(restrict_fw(ctx->L[l], r, bc, ctx->st));
+    CK(cudaMemsetAsync(xc, 0, corner_count(ctx->L[l + 1]) * sizeof(T), ctx->st));
+    CKS(vcycle<T>(ctx, l + 1, bc, xc));
+    CK(prolong_add(ctx->L[l], xc, x, ctx->st));
+    CKS(smooth<T>(ctx, l, b, x, ctx->opts.nu2, true));
+    return MG_OK;
+}
+
+mg_status check_ctx(mg_ctx *ctx) {
+    if (!ctx) {
+        set_err("null context");
+        return MG_ERR_ARG;
+    }
+    if (ctx->broken) {
+        set_err("context unusable after an earlier CUDA failure");
+        return MG_ERR_STATE;
+    }
+    return MG_OK;
+}
+
+mg_status solve_fp64(mg_ctx *ctx, const double *b, double *v, double tol, mg_stats *st) {
+    double bn, rn;
+    CKS(fine_resnorm(ctx, b, v, true, nullptr, 0.0, &bn));
+    st->bnorm = bn;
+    if (bn == 0.0) {
+        CK(zero_interior(ctx->L[0], v, ctx->st));
+        st->rel_resid = 0.0;
+        st->resid_hist[0] = 0.0;
+        return MG_OK;
+    }
+    CKS(fine_resnorm(ctx, b, v, false, nullptr, 0.0, &rn));
+    double rel = rn / bn;
+    st->resid_hist[0] = rel;
+    int it = 0;
+    for (;;) {
+        st->rel_resid = rel;
+        st->cycles = st->outer_iters = it;
+        if (!isfinite(rel)) {
+            set_err("non-finite residual after %d cycles", it);
+            return MG_ERR_NONFINITE;
+        }
+        if (tol > 0.0 && rel <= tol) return MG_OK;
+        if (it >= ctx->opts.max_cycles) {
+            if (tol > 0.0) {
+                set_err("no convergence: relative residual %.3e after %d cycles", rel, it);
+                return MG_ERR_NOCONV;
+            }
+            return MG_OK;
+        }
+        CKS(vcycle<double>(ctx, 0, b, v));
+        it++;
+        CKS(fine_resnorm(ctx, b, v, false, nullptr, 0.0, &rn));
+        rel = rn / bn;
+        if (it < MG_HIST) st->resid_hist[it] = rel;
+    }
+}
+
+// FP32 V-cycles on the correction equation inside FP64 iterative refinement:
+//   r = b - A v (FP64, stored as float(r / s)), e ~ A^{-1} r by
+//   inner_cycles FP32 V-cycles from e = 0, v += s e.
+mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_stats *st) {
+    double bn, rn;
+    CKS(fine_resnorm(ctx, b, v, true, nullptr, 0.0, &bn));
+    st->bnorm = bn;
+    if (bn == 0.0) {
+        CK(zero_interior(ctx->L[0], v, ctx->st));
+        st->rel_resid = 0.0;
+        st->resid_hist[0] = 0.0;
+        return MG_OK;
+    }
+    double scale = bn;
+    CKS(fine_resnorm(ctx, b, v, false, ctx->b32[0], 1.0 / scale, &rn));
+    double rel = rn / bn;
+    st->resid_hist[0] = rel;
+    int outer = 0, cycles = 0;
+    const size_t n0 = corner_count(ctx->L[0]);
+    for (;;) {
+        st->rel_resid = rel;
+        st->cycles = cycles;
+        st->outer_iters = outer;
+        if (!isfinite(rel)) {
+            set_err("non-finite residual after %d refinement steps", outer);
+            return MG_ERR_NONFINITE;
+        }
+        if (tol > 0.0 && rel <= tol) return MG_OK;
+        if (outer >= ctx->opts.max_cycles) {
+            if (tol > 0.0) {
+                set_err("no convergence: relative residual %.3e after %d refinement steps", rel,
+                        outer);
+                return MG_ERR_NOCONV;
+            }
+            return MG_OK;
+        }
+        CK(cudaMemsetAsync(ctx->x32[0], 0, n0 * sizeof(float), ctx->st));
+        for (int c = 0; c < ctx->opts.inner_cycles; c++)
+            CKS(vcycle<float>(ctx, 0, ctx->b32[0], ctx->x32[0]));
+        CK(axpy_f32(ctx->L[0], scale, ctx->x32[0], v, ctx->st));
+        outer++;
+        cycles += ctx->opts.inner_cycles;
+        scale = rn;
+        CKS(fine_resnorm(ctx, b, v, false, ctx->b32[0], 1.0 / scale, &rn));
+        rel = rn / bn;
+        if (outer < MG_HIST) st->resid_hist[outer] = rel;
+    }
+}
+
+StepParams step_params(const mg_ctx *ctx, double dt) {
+    StepParams p;
+    p.nx = ctx->L[0].nx;
+    p.ny = ctx->L[0].ny;
+    p.nz = ctx->L[0].nz;
+    p.h = ctx->h;
+    p.dt = dt;
+    p.lam = ctx->lam;
+    p.mu = ctx->mu;
+    const stz_params &z = ctx->stz;
+    p.tau0 = z.tau0;
+    p.eps0 = z.eps0;
+    p.c0 = z.c0;
+    p.Delta_K = z.Delta_K;
+    p.Omega = z.Omega;
+    p.T = z.T;
+    p.chi_inf = z.chi_inf;
+    p.ez_K = z.ez_K;
+    p.sY = z.sY;
+    p.l = z.l;
+    p.kB = z.kB;
+    return p;
+}
+
+WallParams wall_params(const mg_ctx *ctx, double t) {
+    WallParams w;
+    w.nx = ctx->L[0].nx;
+    w.ny = ctx->L[0].ny;
+    w.nz = ctx->L[0].nz;
+    w.kind = ctx->bc.kind;
+    w.h = ctx->h;
+    w.t = t;
+    w.U_B = ctx->bc.U_B;
+    w.t_ramp = ctx->bc.t_ramp;
+    w.omega = ctx->bc.omega;
+    w.R = ctx->bc.R;
+    w.lambda_w = ctx->bc.lambda_w;
+    return w;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+
+extern "C" {
+
+const char *mg_status_str(mg_status s) {
+    switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_ARG: return "invalid argument";
+    case MG_ERR_SHAPE: return "unsupported grid shape";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_OOM: return "out of device memory";
+    case MG_ERR_NOCONV: return "not converged";
+    case MG_ERR_NONFINITE: return "non-finite residual";
+    case MG_ERR_STATE: return "context unusable";
+    }
+    return "unknown status";
+}
+
+const char *mg_last_error(void) { return g_err; }
+
+void mg_free(mg_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    else cudaDeviceSynchronize();
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->hsum) cudaFreeHost(ctx->hsum);
+    if (ctx->prof_events)
+        for (int i = 0; i < kProfSlots; i++) {
+            cudaEventDestroy(ctx->ev[i][0]);
+            cudaEventDestroy(ctx->ev[i][1]);
+        }
+    delete ctx;
+}
+
+mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc,
+                   const stz_params *stz, const mg_opts *opts, void *stream, mg_ctx **out) {
+    mg_ctx *ctx = nullptr;
+    if (!grid || !moduli || !opts || !out) {
+        set_err("mg_setup: null argument");
+        return MG_ERR_ARG;
+    }
+    *out = nullptr;
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    if (nx < 4 || ny < 4 || nz < 2 || nx % 2 || ny % 2 || nz % 2) {
+        set_err("mg_setup: grid %dx%dx%d unsupported (nx, ny even >= 4; nz even >= 2)", nx, ny, nz);
+        return MG_ERR_SHAPE;
+    }
+    if (!(grid->h > 0.0) || !(moduli->mu > 0.0) || !(moduli->K - 2.0 * moduli->mu / 3.0 + moduli->mu > 0.0)) {
+        set_err("mg_setup: need h > 0, mu > 0 and lambda + mu > 0");
+        return MG_ERR_ARG;
+    }
+    if (opts->precision != MG_FP64 && opts->precision != MG_MIXED) {
+        set_err("mg_setup: precision must be MG_FP64 or MG_MIXED");
+        return MG_ERR_ARG;
+    }
+    if (opts->nu1 < 0 || opts->nu2 < 0 || opts->max_cycles < 0 || opts->max_cycles >= MG_HIST ||
+        (opts->precision == MG_MIXED && opts->inner_cycles < 1)) {
+        set_err("mg_setup: bad nu1/nu2/max_cycles/inner_cycles");
+        return MG_ERR_ARG;
+    }
+    ctx = new mg_ctx();  // value-initialised: every pointer and flag starts at zero
+    ctx->st = (cudaStream_t)stream;
+    ctx->opts = *opts;
+    ctx->h = grid->h;
+    ctx->mu = moduli->mu;
+    ctx->lam = moduli->K - 2.0 * moduli->mu / 3.0;
+    if (bc) {
+        ctx->bc = *bc;
+        ctx->has_bc = true;
+    }
+    if (stz) {
+        ctx->stz = *stz;
+        ctx->has_stz = true;
+    }
+    // hierarchy
+    ctx->L[0] = make_dims(nx, ny, nz);
+    ctx->nlev = 1;
+    while (ctx->nlev < kMaxLev && can_coarsen(ctx->L[ctx->nlev - 1])) {
+        const Dims &p = ctx->L[ctx->nlev - 1];
+        ctx->L[ctx->nlev] = make_dims(p.nx / 2, p.ny / 2, p.nz / 2);
+        ctx->nlev++;
+    }
+    const Dims &dc = ctx->L[ctx->nlev - 1];
+    const long nco = 3L * dc.nx * dc.ny * (dc.nz - 1);
+    if (nco > kMaxCoarse) {
+        set_err("mg_setup: coarsest level %dx%dx%d has %ld unknowns (> %d)", dc.nx, dc.ny, dc.nz,
+                nco, kMaxCoarse);
+        delete ctx;
+        return MG_ERR_SHAPE;
+    }
+    ctx->ncoarse = (int)nco;
+    fine_table(ctx->lam, ctx->mu, ctx->S[0]);
+    for (int l = 1; l < ctx->nlev; l++) galerkin_table(ctx->S[l - 1], ctx->S[l]);
+    const double lp = (ctx->lam + 2.0 * ctx->mu) / ctx->mu, kq = (ctx->lam + ctx->mu) / (4.0 * ctx->mu);
+    ctx->f64.d0 = 2.0 * lp + 4.0;
+    ctx->f64.lp = lp;
+    ctx->f64.kq = kq;
+    ctx->f64.dinv = 1.0 / ctx->f64.d0;
+    ctx->f32.d0 = (float)ctx->f64.d0;
+    ctx->f32.lp = (float)lp;
+    ctx->f32.kq = (float)kq;
+    ctx->f32.dinv = (float)ctx->f64.dinv;
+    for (int l = 0; l < ctx->nlev; l++) {
+        double Di[9];
+        if (!invert3(ctx->S[l] + 13 * 9, Di)) {
+            set_err("mg_setup: singular centre block on level %d", l);
+            delete ctx;
+            return MG_ERR_ARG;
+        }
+        for (int m = 0; m < 243; m++) {
+            ctx->c64[l].S[m] = ctx->S[l][m];
+            ctx->c32[l].S[m] = (float)ctx->S[l][m];
+        }
+        for (int m = 0; m < 9; m++) {
+            ctx->c64[l].Dinv[m] = Di[m];
+            ctx->c32[l].Dinv[m] = (float)Di[m];
+        }
+    }
+    std::vector<double> Ainv;
+    if (!coarse_inverse(dc, ctx->S[ctx->nlev - 1], Ainv)) {
+        set_err("mg_setup: coarsest operator is not positive definite");
+        delete ctx;
+        return MG_ERR_ARG;
+    }
+    // buffers
+    mg_status s = MG_OK;
+#define ALLOC(p, n)                      \
+    do {                                 \
+        s = dalloc(ctx, &(p), (n));      \
+        if (s != MG_OK) goto fail;       \
+    } while (0)
+    for (int l = 0; l < ctx->nlev; l++) {
+        const size_t n = corner_count(ctx->L[l]);
+        if (l > 0) {
+            ALLOC(ctx->x64[l], n);
+            ALLOC(ctx->b64[l], n);
+        }
+        ALLOC(ctx->r64[l], n);
+        ALLOC(ctx->x32[l], n);
+        ALLOC(ctx->b32[l], n);
+        ALLOC(ctx->r32[l], n);
+    }
+    ALLOC(ctx->Ainv, Ainv.size());
+    ALLOC(ctx->partials, (size_t)kRedBlocks);
+    ALLOC(ctx->dsum, (size_t)1);
+    {
+        const size_t nc = (size_t)nx * ny * nz;
+        ALLOC(ctx->sig_star, 6 * nc);
+        ALLOC(ctx->dpl, nc);
+        ALLOC(ctx->sbar, nc);
+        ALLOC(ctx->chi_tmp, nc);
+        ALLOC(ctx->rhs, corner_count(ctx->L[0]));
+    }
+#undef ALLOC
+    if (cudaMallocHost((void **)&ctx->hsum, sizeof(double)) != cudaSuccess) {
+        set_err("cudaMallocHost failed");
+        s = MG_ERR_OOM;
+        goto fail;
+    }
+    if (cudaMemcpyAsync(ctx->Ainv, Ainv.data(), Ainv.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, ctx->st) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+        set_err("mg_setup: upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        s = MG_ERR_CUDA;
+        goto fail;
+    }
+    *out = ctx;
+    return MG_OK;
+fail:
+    mg_free(ctx);
+    return s;
+}
+
+mg_status mg_solve(mg_ctx *ctx, const double *rhs, double *v, double tol, mg_stats *stats) {
+    CKS(check_ctx(ctx));
+    if (!rhs || !v) {
+        set_err("mg_solve: null array");
+        return MG_ERR_ARG;
+    }
+    mg_stats local;
+    mg_stats *st = stats ? stats : &local;
+    memset(st, 0, sizeof(*st));
+    if (ctx->opts.precision == MG_FP64) return solve_fp64(ctx, rhs, v, tol, st);
+    return solve_mixed(ctx, rhs, v, tol, st);
+}
+
+mg_status qs_step(mg_ctx *ctx, qs_state *state, double dt, double tol, mg_stats *stats) {
+    CKS(check_ctx(ctx));
+    if (!state || !state->v || !state->sigma || !state->chi || !(dt > 0.0)) {
+        set_err("qs_step: null state array or dt <= 0");
+        return MG_ERR_ARG;
+    }
+    if (!ctx->has_stz || !ctx->has_bc) {
+        set_err("qs_step: context was set up without stz/bc parameters");
+        return MG_ERR_ARG;
+    }
+    const StepParams p = step_params(ctx, dt);
+    CK(stress_predict(p, state->v, state->sigma, state->chi, ctx->sig_star, ctx->dpl, ctx->sbar,
+                      ctx->st));
+    CK(chi_update(p, state->sigma, state->chi, ctx->dpl, ctx->sbar, ctx->chi_tmp, ctx->st));
+    CK(wall_fill(wall_params(ctx, state->t + dt), state->v, ctx->st));
+    CK(div_rhs(p, ctx->sig_star, ctx->rhs, ctx->st));
+    const mg_status s = mg_solve(ctx, ctx->rhs, state->v, tol, stats);
+    if (s == MG_ERR_CUDA || s == MG_ERR_STATE || s == MG_ERR_ARG) return s;
+    CK(stress_correct(p, state->v, ctx->sig_star, state->sigma, ctx->chi_tmp, state->chi, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    state->t += dt;
+    state->step += 1;
+    return s;
+}
+
+// ------------------------------------------------------------ components
+
+int mg_num_levels(const mg_ctx *ctx) { return ctx ? ctx->nlev : 0; }
+
+mg_status mg_level_dims(const mg_ctx *ctx, int level, int *dims) {
+    if (!ctx || !dims || level < 0 || level >= ctx->nlev) {
+        set_err("mg_level_dims: bad argument");
+        return MG_ERR_ARG;
+    }
+    dims[0] = ctx->L[level].nx;
+    dims[1] = ctx->L[level].ny;
+    dims[2] = ctx->L[level].nz;
+    return MG_OK;
+}
+
+mg_status mg_level_stencil(const mg_ctx *ctx, int level, double *host_S) {
+    if (!ctx || !host_S || level < 0 || level >= ctx->nlev) {
+        set_err("mg_level_stencil: bad argument");
+        return MG_ERR_ARG;
+    }
+    memcpy(host_S, ctx->S[level], 243 * sizeof(double));
+    return MG_OK;
+}
+
+static mg_status level_arg(mg_ctx *ctx, int level, int need_coarser) {
+    CKS(check_ctx(ctx));
+    if (level < 0 || level >= ctx->nlev - (need_coarser ? 1 : 0)) {
+        set_err("bad level %d", level);
+        return MG_ERR_ARG;
+    }
+    return MG_OK;
+}
+
+mg_status mg_residual(mg_ctx *ctx, int level, const double *b, const double *x, double *r) {
+    CKS(level_arg(ctx, level, 0));
+    if (!b || !x || !r || r == x) {
+        set_err("mg_residual: bad arrays");
+        return MG_ERR_ARG;
+    }
+    CKS(residual_level<double>(ctx, level, b, x, r));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps, int descending,
+                    int precision) {
+    CKS(level_arg(ctx, level, 0));
+    if (!b || !x || nsweeps < 0) {
+        set_err("mg_smooth: bad arguments");
+        return MG_ERR_ARG;
+    }
+    if (precision == MG_FP64)
+        CKS(smooth<double>(ctx, level, (const double *)b, (double *)x, nsweeps, descending != 0));
+    else
+        CKS(smooth<float>(ctx, level, (const float *)b, (float *)x, nsweeps, descending != 0));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+mg_status mg_restrict(mg_ctx *ctx, int level, const double *r, double *bc) {
+    CKS(level_arg(ctx, level, 1));
+    if (!r || !bc) {
+        set_err("mg_restrict: null array");
+        return MG_ERR_ARG;
+    }
+    CK(cudaMemsetAsync(bc, 0, corner_count(ctx->L[level + 1]) * sizeof(double), ctx->st));
+    CK(restrict_fw(ctx->L[level], r, bc, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+mg_status mg_prolong_add(mg_ctx *ctx, int level, const double *xc, double *x) {
+    CKS(level_arg(ctx, level, 1));
+    if (!xc || !x) {
+        set_err("mg_prolong_add: null array");
+        return MG_ERR_ARG;
+    }
+    CK(prolong_add(ctx->L[level], xc, x, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+mg_status mg_vcycle(mg_ctx *ctx, const double *b, double *x) {
+    CKS(check_ctx(ctx));
+    if (!b || !x) {
+        set_err("mg_vcycle: null array");
+        return MG_ERR_ARG;
+    }
+    CKS(vcycle<double>(ctx, 0, b, x));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+static mg_status step_arg(mg_ctx *ctx) {
+    CKS(check_ctx(ctx));
+    if (!ctx->has_stz) {
+        set_err("context was set up without stz parameters");
+        return MG_ERR_ARG;
+    }
+    return MG_OK;
+}
+
+mg_status qs_stress_predict(mg_ctx *ctx, const double *v, const double *sigma, const double *chi,
+                            double dt, double *sigma_star, double *dpl, double *sbar) {
+    CKS(step_arg(ctx));
+    CK(stress_predict(step_params(ctx, dt), v, sigma, chi, sigma_star, dpl, sbar, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+mg_status qs_chi_update(mg_ctx *ctx, const double *sigma, const double *chi, const double *dpl,
+                        const double *sbar, double dt, double *chi_new) {
+    CKS(step_arg(ctx));
+    CK(chi_update(step_params(ctx, dt), sigma, chi, dpl, sbar, chi_new, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+mg_status qs_rhs(mg_ctx *ctx, const double *sigma_star, double dt, double *b) {
+    CKS(check_ctx(ctx));
+    CK(div_rhs(step_params(ctx, dt), sigma_star, b, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+mg_status qs_stress_correct(mg_ctx *ctx, const double *v, const double *sigma_star, double dt,
+                            double *sigma) {
+    CKS(check_ctx(ctx));
+    CK(stress_correct(step_params(ctx, dt), v, sigma_star, sigma, nullptr, nullptr, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+mg_status qs_wall_fill(mg_ctx *ctx, double *v, double t) {
+    CKS(check_ctx(ctx));
+    if (!ctx->has_bc) {
+        set_err("context was set up without bc parameters");
+        return MG_ERR_ARG;
+    }
+    CK(wall_fill(wall_params(ctx, t), v, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+// ------------------------------------------------------------ measurement
+
+mg_status mg_profile(mg_ctx *ctx, int enable) {
+    CKS(check_ctx(ctx));
+    CK(cudaStreamSynchronize(ctx->st));
+    CKS(prof_drain(ctx));
+    if (enable && !ctx->prof_events) {
+        for (int i = 0; i < kProfSlots; i++) {
+            CK(cudaEventCreate(&ctx->ev[i][0]));
+            CK(cudaEventCreate(&ctx->ev[i][1]));
+        }
+        ctx->prof_events = true;
+    }
+    ctx->prof_on = enable != 0;
+    ctx->prof_ms = 0.0;
+    ctx->prof_sweeps = ctx->prof_launches = 0;
+    return MG_OK;
+}
+
+mg_status mg_profile_read(mg_ctx *ctx, double *smooth_ms, long *smooth_sweeps,
+                          long *smooth_launches) {
+    CKS(check_ctx(ctx));
+    CK(cudaStreamSynchronize(ctx->st));
+    CKS(prof_drain(ctx));
+    if (smooth_ms) *smooth_ms = ctx->prof_ms;
+    if (smooth_sweeps) *smooth_sweeps = ctx->prof_sweeps;
+    if (smooth_launches) *smooth_launches = ctx->prof_launches;
+    return MG_OK;
+}
+
+long mg_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// qsmg_impl.h -- internal declarations shared by the library's translation
+// units (kernels and host orchestration).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+namespace qsmg {
+
+// kernels launched by this library (read through mg_launch_count)
+extern std::atomic<long> g_launches;
+inline void count_launch(long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// cell dimensions of one level; corner arrays are (3, nz+1, ny, nx)
+struct Dims {
+    int nx, ny, nz;
+    long cs;  // component stride (nz+1)*ny*nx
+};
+
+inline Dims make_dims(int nx, int ny, int nz) {
+    Dims d;
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = nz;
+    d.cs = (long)(nz + 1) * ny * nx;
+    return d;
+}
+
+// Finest-level operator, Eq. (30) with the collocated stencils of section
+// 3.4, scaled by -h^2/(mu dt): centre d0 = (2 lam + 8 mu)/mu on the diagonal,
+// face neighbour along the component's own axis -lp = -(lam+2mu)/mu, along
+// the other axes -1, edge neighbours -kq * sa * sb with kq = (lam+mu)/(4 mu).
+template <typename T>
+struct Fine {
+    T d0, lp, kq, dinv;
+};
+
+// Coarse-level operator: one constant 27-point stencil of 3x3 blocks
+// (Galerkin product, Eq. 36) plus the inverse of its centre block.
+// Passed to kernels by value (lives in the kernel-parameter constant bank).
+template <typename T>
+struct Coarse {
+    T S[243];
+    T Dinv[9];
+};
+
+// fixed reduction geometry: partial sums per block, then one block adds them
+// in a fixed order, so every norm is bitwise reproducible
+constexpr int kRedBlocks = 1216;  // 8 x 152 SMs
+constexpr int kRedThreads = 256;
+
+// ---------------------------------------------------------------- multigrid
+cudaError_t gs_colour_fine(const Dims &d, const Fine<double> &f, const double *b, double *x,
+                           int colour, cudaStream_t s);
+cudaError_t gs_colour_fine(const Dims &d, const Fine<float> &f, const float *b, float *x,
+                           int colour, cudaStream_t s);
+cudaError_t gs_colour_coarse(const Dims &d, const Coarse<double> &c, const double *b, double *x,
+                             int colour, cudaStream_t s);
+cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float *b, float *x,
+                             int colour, cudaStream_t s);
+
+// r = b - A x (interior), r walls zero
+cudaError_t residual_fine(const Dims &d, const Fine<double> &f, const double *b, const double *x,
+                          double *r, cudaStream_t s);
+cudaError_t residual_fine(const Dims &d, const Fine<float> &f, const float *b, const float *x,
+                          float *r, cudaStream_t s);
+cudaError_t residual_coarse(const Dims &d, const Coarse<double> &c, const double *b,
+                            const double *x, double *r, cudaStream_t s);
+cudaError_t residual_coarse(const Dims &d, const Coarse<float> &c, const float *b, const float *x,
+                            float *r, cudaStream_t s);
+
+// FP64 fine residual with the sum of squares into partials[kRedBlocks];
+// wall_only treats interior x as zero (lifted right-hand side);
+// r32 (optional) receives float(r * out_scale)
+cudaError_t residual_norm_fine64(const Dims &d, const Fine<double> &f, const double *b,
+                                 const double *x, bool wall_only, float *r32, double out_scale,
+                                 double *partials, cudaStream_t s);
+// sum of squares of a level vector's interior into partials
+cudaError_t sumsq(const Dims &d, const double *r, double *partials, cudaStream_t s);
+// out[0] = sum of partials[0..kRedBlocks)
+cudaError_t sum_partials(const double *partials, double *out, cudaStream_t s);
+
+cudaError_t restrict_fw(const Dims &fine, const double *r, double *bc, cudaStream_t s);
+cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_t s);
+cudaError_t prolong_add(const Dims &fine, const double *xc, double *x, cudaStream_t s);
+cudaError_t prolong_add(const Dims &fine, const float *xc, float *x, cudaStream_t s);
+
+// x += Ainv r on the coarsest level (dense FP64 inverse, n unknowns)
+cudaError_t coarse_solve(const Dims &d, const double *Ainv, int n, const double *r, double *x,
+                         cudaStream_t s);
+cudaError_t coarse_solve(const Dims &d, const double *Ainv, int n, const float *r, float *x,
+                         cudaStream_t s);
+
+cudaError_t zero_interior(const Dims &d, double *x, cudaStream_t s);
+// v += scale * e (interior)
+cudaError_t axpy_f32(const Dims &d, double scale, const float *e, double *v, cudaStream_t s);
+
+// ---------------------------------------------------------------- step
+struct StepParams {
+    int nx, ny, nz;
+    double h, dt, lam, mu;
+    double tau0, eps0, c0, Delta_K, Omega, T, chi_inf, ez_K, sY, l, kB;
+};
+struct WallParams {
+    int nx, ny, nz, kind;
+    double h, t, U_B, t_ramp, omega, R, lambda_w;
+};
+
+cudaError_t stress_predict(const StepParams &p, const double *v, const double *sig,
+                           const double *chi, double *sig_star, double *dpl, double *sbar,
+                           cudaStream_t s);
+cudaError_t chi_update(const StepParams &p, const double *sig, const double *chi,
+                       const double *dpl, const double *sbar, double *chi_new, cudaStream_t s);
+cudaError_t div_rhs(const StepParams &p, const double *sig_star, double *b, cudaStream_t s);
+// sigma = sigma* + dt C:D(v); if chi_src is given also chi_dst = chi_src
+cudaError_t stress_correct(const StepParams &p, const double *v, const double *sig_star,
+                           double *sig, const double *chi_src, double *chi_dst, cudaStream_t s);
+cudaError_t wall_fill(const WallParams &w, double *v, cudaStream_t s);
+
+}  // namespace qsmg

@@ -1,0 +1,295 @@
+// step_kernels.cu -- pointwise kernels of the quasi-static projection step
+// (section 3.3): stress predictor with the STZ rate, effective temperature,
+// right-hand side of the projection system, stress correction, wall fill.
+//
+// Cell arrays (nz, ny, nx); stress (6, nz, ny, nx) in the order xx, yy, zz,
+// yz, xz, xy; corner arrays (3, nz+1, ny, nx).  x and y are periodic.
+#include "qsmg_impl.h"
+
+namespace qsmg {
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned nblocks(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+struct StzConst {
+    double eDT_over_tau0;  // exp(-Delta/(kB T)) / tau0
+    double beta;           // Omega eps0 / (kB T)
+    double sY, ez_K;
+};
+
+__host__ StzConst stz_const(const StepParams &p) {
+    StzConst c;
+    c.eDT_over_tau0 = exp(-p.Delta_K / p.T) / p.tau0;
+    c.beta = p.Omega * p.eps0 / (p.kB * p.T);
+    c.sY = p.sY;
+    c.ez_K = p.ez_K;
+    return c;
+}
+
+// athermal STZ rate magnitude, Eqs. (20)-(22):
+// D = exp(-e_z/(kB chi)) exp(-Delta/(kB T)) cosh(Omega eps0 sbar/(kB T)) (1 - s_Y/sbar) / tau0
+// and 0 at or below yield (or for chi <= 0)
+__device__ __forceinline__ double stz_rate(const StzConst &c, double sbar, double chi) {
+    if (!(sbar > c.sY) || !(chi > 0.0)) return 0.0;
+    return exp(-c.ez_K / chi) * c.eDT_over_tau0 * cosh(c.beta * sbar) * (1.0 - c.sY / sbar);
+}
+
+// sbar with sbar^2 = 1/2 sigma0 : sigma0
+__device__ __forceinline__ double sbar_of(const double s[6]) {
+    const double m = (s[0] + s[1] + s[2]) * (1.0 / 3.0);
+    const double d0 = s[0] - m, d1 = s[1] - m, d2 = s[2] - m;
+    const double q = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+    return sqrt(0.5 * q);
+}
+
+// Eq. (31): G[a][b] = d v_a / d x_b at the centre of cell (i, j, k), from its
+// 8 corners; each derivative averages the 4 edge differences along its axis
+__device__ __forceinline__ void cell_gradient(const double *__restrict__ v, int nx, int ny, int nz,
+                                              double inv4h, int i, int j, int k, double G[3][3]) {
+    const long cs = (long)(nz + 1) * ny * nx;
+    const int i1 = (i + 1 < nx) ? i + 1 : 0, j1 = (j + 1 < ny) ? j + 1 : 0;
+    const long p000 = ((long)k * ny + j) * nx + i, p100 = ((long)k * ny + j) * nx + i1;
+    const long p010 = ((long)k * ny + j1) * nx + i, p110 = ((long)k * ny + j1) * nx + i1;
+    const long pl = (long)ny * nx;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double *g = v + a * cs;
+        const double c000 = g[p000], c100 = g[p100], c010 = g[p010], c110 = g[p110];
+        const double c001 = g[p000 + pl], c101 = g[p100 + pl], c011 = g[p010 + pl],
+                     c111 = g[p110 + pl];
+        G[a][0] = ((c100 - c000) + (c110 - c010) + (c101 - c001) + (c111 - c011)) * inv4h;
+        G[a][1] = ((c010 - c000) + (c110 - c100) + (c011 - c001) + (c111 - c101)) * inv4h;
+        G[a][2] = ((c001 - c000) + (c101 - c100) + (c011 - c010) + (c111 - c110)) * inv4h;
+    }
+}
+
+// Eq. (27): sigma* = sigma + dt (L sigma + sigma L^T - tr(L) sigma - 2 mu D^pl sigma0 / sbar)
+__global__ void k_stress_predict(StepParams p, StzConst c, const double *__restrict__ v,
+                                 const double *__restrict__ sig, const double *__restrict__ chi,
+                                 double *__restrict__ sig_star, double *__restrict__ dpl,
+                                 double *__restrict__ sbar_out, long nc) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nc) return;
+    const int i = (int)(q % p.nx);
+    const long r = q / p.nx;
+    const int j = (int)(r % p.ny), k = (int)(r / p.ny);
+    double G[3][3];
+    cell_gradient(v, p.nx, p.ny, p.nz, 0.25 / p.h, i, j, k, G);
+    double s6[6];
+#pragma unroll
+    for (int a = 0; a < 6; a++) s6[a] = sig[a * nc + q];
+    // full symmetric matrix
+    const double S[3][3] = {{s6[0], s6[5], s6[4]}, {s6[5], s6[1], s6[3]}, {s6[4], s6[3], s6[2]}};
+    const double sb = sbar_of(s6);
+    const double D = stz_rate(c, sb, chi[q]);
+    const double trL = G[0][0] + G[1][1] + G[2][2];
+    const double m = (s6[0] + s6[1] + s6[2]) * (1.0 / 3.0);
+    const double pl = (D > 0.0) ? 2.0 * p.mu * D / sb : 0.0;
+    // (a, b) pairs of the 6 stored components
+    const int ia[6] = {0, 1, 2, 1, 0, 0}, ib[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+    for (int n = 0; n < 6; n++) {
+        const int a = ia[n], b = ib[n];
+        double rate = -trL * S[a][b];
+#pragma unroll
+        for (int e = 0; e < 3; e++) rate += G[a][e] * S[e][b] + S[a][e] * G[b][e];
+        rate -= pl * (S[a][b] - (a == b ? m : 0.0));
+        sig_star[n * nc + q] = S[a][b] + p.dt * rate;
+    }
+    dpl[q] = D;
+    sbar_out[q] = sb;
+}
+
+// Eq. (26): chi' = chi + (dt/c0)[ (2 D sbar / s_Y)(chi_inf - chi) + l^2 div(D grad chi) ]
+// diffusion: sum over the 6 faces of (D_P + D_N)/2 (chi_N - chi_P) / h^2;
+// z ghost cells carry linearly extrapolated sigma and chi, and their D is
+// the STZ rate of those extrapolated values
+__global__ void k_chi_update(StepParams p, StzConst c, const double *__restrict__ sig,
+                             const double *__restrict__ chi, const double *__restrict__ dpl,
+                             const double *__restrict__ sbar, double *__restrict__ chi_new,
+                             long nc) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nc) return;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int i = (int)(q % nx);
+    const long r = q / nx;
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const long pl = (long)nx * ny;
+    const int ip = (i + 1 < nx) ? i + 1 : 0, im = i ? i - 1 : nx - 1;
+    const int jp = (j + 1 < ny) ? j + 1 : 0, jm = j ? j - 1 : ny - 1;
+    const long base = (long)k * pl + (long)j * nx;
+    const double c0 = chi[q], D0 = dpl[q];
+    double acc = 0.0;
+    long nb[4] = {base + ip, base + im, (long)k * pl + (long)jp * nx + i,
+                  (long)k * pl + (long)jm * nx + i};
+#pragma unroll
+    for (int n = 0; n < 4; n++) acc += 0.5 * (D0 + dpl[nb[n]]) * (chi[nb[n]] - c0);
+    // z neighbours, with ghosts at the walls
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+        const int kn = side ? k + 1 : k - 1;
+        double cn, Dn;
+        if (kn >= 0 && kn < nz) {
+            cn = chi[q + (side ? pl : -pl)];
+            Dn = dpl[q + (side ? pl : -pl)];
+        } else {
+            // ghost: 2 * (this layer) - (next layer inward)
+            const long q1 = q + (side ? -pl : pl);
+            double s6[6];
+#pragma unroll
+            for (int a = 0; a < 6; a++) s6[a] = 2.0 * sig[a * nc + q] - sig[a * nc + q1];
+            cn = 2.0 * c0 - chi[q1];
+            Dn = stz_rate(c, sbar_of(s6), cn);
+        }
+        acc += 0.5 * (D0 + Dn) * (cn - c0);
+    }
+    const double growth = 2.0 * D0 * sbar[q] / p.sY * (p.chi_inf - c0);
+    chi_new[q] = c0 + p.dt / p.c0 * (growth + (p.l * p.l) / (p.h * p.h) * acc);
+}
+
+// b = (h^2/(mu dt)) div sigma* at interior corners; the corner derivative is
+// Eq. (31) shifted by half a cell: cells (i-1..i, j-1..j, k-1..k)
+__global__ void k_div_rhs(StepParams p, const double *__restrict__ ss, double *__restrict__ b,
+                          long tot, double scale) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot) return;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int i = (int)(t % nx);
+    const long r = t / nx;
+    const int j = (int)(r % ny), k = (int)(r / ny) + 1;
+    const int im = i ? i - 1 : nx - 1, jm = j ? j - 1 : ny - 1;
+    const long nc = (long)nx * ny * nz, pl = (long)nx * ny;
+    // the 8 surrounding cells c[dk][dj][di], d = 0 is the lower neighbour
+    const long kb0 = (long)(k - 1) * pl, kb1 = (long)k * pl;
+    const long rj0 = (long)jm * nx, rj1 = (long)j * nx;
+    const long cc[2][2][2] = {{{kb0 + rj0 + im, kb0 + rj0 + i}, {kb0 + rj1 + im, kb0 + rj1 + i}},
+                              {{kb1 + rj0 + im, kb1 + rj0 + i}, {kb1 + rj1 + im, kb1 + rj1 + i}}};
+    // stored component of sigma_ab
+    const int comp[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    const long cs = (long)(nz + 1) * pl;
+    const long node = (long)k * pl + (long)j * nx + i;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double *fx = ss + comp[a][0] * nc, *fy = ss + comp[a][1] * nc,
+                     *fz = ss + comp[a][2] * nc;
+        double s = 0.0;
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+#pragma unroll
+            for (int w = 0; w < 2; w++) {
+                s += fx[cc[u][w][1]] - fx[cc[u][w][0]];
+                s += fy[cc[u][1][w]] - fy[cc[u][0][w]];
+                s += fz[cc[1][u][w]] - fz[cc[0][u][w]];
+            }
+        b[a * cs + node] = scale * s;
+    }
+}
+
+// Eq. (29): sigma = sigma* + dt (lam tr(D) I + 2 mu D), D = sym grad v
+__global__ void k_stress_correct(StepParams p, const double *__restrict__ v,
+                                 const double *__restrict__ ss, double *__restrict__ sig,
+                                 const double *__restrict__ chi_src, double *__restrict__ chi_dst,
+                                 long nc) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nc) return;
+    const int i = (int)(q % p.nx);
+    const long r = q / p.nx;
+    const int j = (int)(r % p.ny), k = (int)(r / p.ny);
+    double G[3][3];
+    cell_gradient(v, p.nx, p.ny, p.nz, 0.25 / p.h, i, j, k, G);
+    const double tr = G[0][0] + G[1][1] + G[2][2];
+    const double dt = p.dt, lam = p.lam, mu = p.mu;
+    sig[0 * nc + q] = ss[0 * nc + q] + dt * (lam * tr + 2.0 * mu * G[0][0]);
+    sig[1 * nc + q] = ss[1 * nc + q] + dt * (lam * tr + 2.0 * mu * G[1][1]);
+    sig[2 * nc + q] = ss[2 * nc + q] + dt * (lam * tr + 2.0 * mu * G[2][2]);
+    sig[3 * nc + q] = ss[3 * nc + q] + dt * mu * (G[1][2] + G[2][1]);
+    sig[4 * nc + q] = ss[4 * nc + q] + dt * mu * (G[0][2] + G[2][0]);
+    sig[5 * nc + q] = ss[5 * nc + q] + dt * mu * (G[0][1] + G[1][0]);
+    if (chi_dst) chi_dst[q] = chi_src[q];
+}
+
+// wall velocities of section 4 (simple shear with ramp) and section 5 (disc)
+__global__ void k_wall_fill(WallParams w, double *__restrict__ v) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long pl = (long)w.nx * w.ny;
+    if (t >= pl) return;
+    const int i = (int)(t % w.nx), j = (int)(t / w.nx);
+    double top[3] = {0.0, 0.0, 0.0}, bot[3] = {0.0, 0.0, 0.0};
+    if (w.kind == 0) {
+        const double U = (w.t < w.t_ramp) ? w.U_B * w.t / w.t_ramp : w.U_B;
+        top[0] = U;
+        bot[0] = -U;
+    } else {
+        const double L = 0.5 * w.nx * w.h;
+        const double x = -L + i * w.h, y = -0.5 * w.ny * w.h + j * w.h;
+        const double r2 = (x * x + y * y) / (L * L), R2 = w.R * w.R;
+        const double f = (r2 < R2) ? 1.0 : exp(-w.lambda_w * (r2 - R2) * (r2 - R2));
+        top[0] = -w.omega * y * f;
+        top[1] = w.omega * x * f;
+        const double sgn = (w.kind == 2) ? 1.0 : (w.kind == 3 ? -1.0 : 0.0);
+        bot[0] = sgn * top[0];
+        bot[1] = sgn * top[1];
+    }
+    const long cs = (long)(w.nz + 1) * pl;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        v[a * cs + t] = bot[a];
+        v[a * cs + (long)w.nz * pl + t] = top[a];
+    }
+}
+
+}  // namespace
+
+cudaError_t stress_predict(const StepParams &p, const double *v, const double *sig,
+                           const double *chi, double *sig_star, double *dpl, double *sbar,
+                           cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    k_stress_predict<<<nblocks(nc), kThreads, 0, s>>>(p, stz_const(p), v, sig, chi, sig_star, dpl,
+                                                      sbar, nc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t chi_update(const StepParams &p, const double *sig, const double *chi,
+                       const double *dpl, const double *sbar, double *chi_new, cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    k_chi_update<<<nblocks(nc), kThreads, 0, s>>>(p, stz_const(p), sig, chi, dpl, sbar, chi_new,
+                                                  nc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t div_rhs(const StepParams &p, const double *sig_star, double *b, cudaStream_t s) {
+    const long pl = (long)p.nx * p.ny;
+    const long tot = pl * (p.nz - 1);
+    const double scale = p.h * p.h / (p.mu * p.dt) * (0.25 / p.h);
+    cudaError_t e;
+    const long cs = (long)(p.nz + 1) * pl;
+    for (int a = 0; a < 3; a++) {  // wall planes of b are not part of the system
+        e = cudaMemsetAsync(b + a * cs, 0, pl * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(b + a * cs + (long)p.nz * pl, 0, pl * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+    }
+    k_div_rhs<<<nblocks(tot), kThreads, 0, s>>>(p, sig_star, b, tot, scale);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t stress_correct(const StepParams &p, const double *v, const double *sig_star,
+                           double *sig, const double *chi_src, double *chi_dst, cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    k_stress_correct<<<nblocks(nc), kThreads, 0, s>>>(p, v, sig_star, sig, chi_src, chi_dst, nc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t wall_fill(const WallParams &w, double *v, cudaStream_t s) {
+    const long pl = (long)w.nx * w.ny;
+    k_wall_fill<<<nblocks(pl), kThreads, 0, s>>>(w, v);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace qsmg

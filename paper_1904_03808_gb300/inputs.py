@@ -74,18 +74,11 @@ def chi_field(seed: int, nx: int, ny: int, nz: int, mean: float, std: float,
     c = (g.size - 1) // 2
     nzp = nz + 2 * c
     w = normal_noise(seed, nzp * ny * nx).reshape(nzp, ny, nx)
+    from scipy.ndimage import correlate1d
     # x and y: periodic wrap; z: the padded shell supplies the out-of-range terms
-    acc = np.zeros_like(w)
-    for t, gt in enumerate(g):
-        acc += gt * np.roll(w, c - t, axis=2)
-    w = acc
-    acc = np.zeros_like(w)
-    for t, gt in enumerate(g):
-        acc += gt * np.roll(w, c - t, axis=1)
-    w = acc
-    out = np.zeros((nz, ny, nx))
-    for t, gt in enumerate(g):
-        out += gt * w[t:t + nz]
+    w = correlate1d(w, g, axis=2, mode="wrap")
+    w = correlate1d(w, g, axis=1, mode="wrap")
+    out = correlate1d(w, g, axis=0, mode="constant")[c:c + nz]
     # N = sqrt(sum over the cutoff box of exp(-2|r|^2/l_c^2)) = (sum g_d^2)^(3/2)
     norm = float(np.sum(g * g)) ** 1.5
     return mean + std * out / norm
