@@ -175,9 +175,13 @@ def test_fp64_solve_matches_oracle_equal_cycles(shape):
     assert rel(c(vg), vo) <= TOL64
     # residual histories: rounding of r = b - A v is ~eps |A| |v| per entry, so
     # late entries (near 1e-10) agree only to a few digits
+    # (entries at the round-off floor, as after a direct solve on a single-level
+    # grid, are compared in absolute terms)
     gh = np.array(s.resid_hist[:cyc + 1])
-    assert np.allclose(gh[:4], hist[:4], rtol=1e-9, atol=0)
-    assert np.allclose(gh, hist, rtol=5e-2, atol=0)
+    big = hist > 1e-12
+    assert np.allclose(gh[:4][big[:4]], hist[:4][big[:4]], rtol=1e-9, atol=0)
+    assert np.allclose(gh[big], hist[big], rtol=5e-2, atol=0)
+    assert np.all(gh[~big] <= 1e-12)
     # and to tolerance directly: the same cycle count up to a borderline cycle
     ctx2 = ctx_for(shape, max_cycles=100)
     vg2 = g(v)
@@ -237,7 +241,8 @@ def test_zero_rhs_gives_zero_and_status_codes():
 # --------------------------------------------------------------- step kernels
 
 def _stz_state(n, nz=None, seed=3, preload=1.5e9):
-    w = I.Workload(n, steps=10, strain=0.04, preload=preload, nz=nz, seed=seed)
+    # strain 2% over 10 steps keeps chi physical (below ~700 K) in every test
+    w = I.Workload(n, steps=10, strain=0.02, preload=preload, nz=nz, seed=seed)
     v, sig, chi, t = w.initial_state()
     rng = np.random.default_rng(seed)
     v[:, 1:w.nz] += 1e-3 * w.U_B * rng.normal(size=v[:, 1:w.nz].shape)
@@ -285,11 +290,15 @@ def test_disc_wall_fill(kind):
     vg = g(v)
     ctx.wall_fill(vg, 5.0)
     O.wall_fill(v, w.h, O.BC(**w.bc_values()), 5.0)
-    assert np.allclose(c(vg), v, rtol=1e-15, atol=0)
+    # exp() of the CUDA and C libraries may differ by an ulp, and a fused
+    # multiply-add leaves ~1e-20 where x = -L + i h is exactly zero on the CPU
+    assert np.allclose(c(vg), v, rtol=1e-13, atol=1e-13 * np.abs(v).max())
 
 
-@pytest.mark.parametrize("preload,n,nz,steps", [(1.5e9, 16, None, 6), (0.0, 16, None, 4),
-                                                 (1.2e9, 24, 8, 5), (1.5e9, 32, None, 4)])
+# multi-step runs use a 1.2 GPa preload: at 1.5 GPa the forward-Euler STZ
+# update overshoots in the hottest cells (2 mu D dt / sbar > 2) and diverges
+@pytest.mark.parametrize("preload,n,nz,steps", [(1.2e9, 16, None, 6), (0.0, 16, None, 4),
+                                                 (1.2e9, 24, 8, 5), (1.2e9, 32, None, 4)])
 def test_qs_step_trajectory(preload, n, nz, steps):
     """Whole steps, warm-started solves, FP64: the GPU runs the oracle's cycle
     count each step (tol = 0 with max_cycles = oracle cycles)."""
@@ -316,7 +325,7 @@ def test_qs_step_trajectory(preload, n, nz, steps):
 
 
 def test_qs_step_mixed_tracks_fp64():
-    w, v, sig, chi, t = _stz_state(32, preload=1.5e9)
+    w, v, sig, chi, t = _stz_state(32, preload=1.2e9)
     shape = (w.nx, w.ny, w.nz)
     mg = O.MG(*shape, LAM, MU)
     p = O.STZ(**w.stz)
