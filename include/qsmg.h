@@ -231,6 +231,42 @@ mg_status mg_profile_read(mg_ctx *ctx, double *smooth_ms, long *smooth_sweeps,
 /* Kernels this library has launched since it was loaded (all contexts). */
 long mg_launch_count(void);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free entry point (no counterpart in the paper)           */
+/* ------------------------------------------------------------------ */
+
+/*
+ * mg_residual_restrict_static -- bc = T^T (b - Ahat x) on the finest level of
+ * an nx*ny*nz grid: the residual and full-weighting restriction kernels of the
+ * V-cycle, for callers that cannot allocate device memory.  It needs no
+ * context and calls no cudaMalloc, cudaFree or other allocating routine:
+ * the intermediate fine-level residual lives in one fixed array compiled into
+ * this library.  It serves callers whose device memory belongs to another
+ * allocator with a fixed budget (a host framework's memory pool that must not
+ * see hidden allocations), and callers on a latency-critical path where the
+ * implicit device-wide synchronisation of cudaFree is not acceptable.
+ *   grid, moduli: as for mg_setup (nx, ny even >= 4; nz even >= 2).
+ *   b, x: device (3, nz+1, ny, nx); x carries the wall values.
+ *   bc: device (3, nz/2+1, ny/2, nx/2); its interior receives T^T r, its wall
+ *       planes are set to zero.
+ *   stream: a cudaStream_t; the work is enqueued there and the call returns
+ *       when that stream has finished it.
+ * Limit: the array holds 2097152 doubles (16 MiB), so 3 (nz+1) ny nx must not
+ * exceed 2097152 (e.g. 64^3 fits, 96^3 does not); larger grids return
+ * MG_ERR_SHAPE with a message.  Every GPU that loads the library holds the
+ * array until the process exits.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.
+ * All calls share the one array, which keeps the last call's residual (every
+ * value a call reads was written by the same call): calls that overlap on the
+ * GPU, from other streams or host threads, race on it, so serialise them.
+ * Errors: MG_ERR_ARG, MG_ERR_SHAPE, MG_ERR_CUDA.
+ */
+mg_status mg_residual_restrict_static(const mg_grid *grid, const mg_moduli *moduli,
+                                      const double *b, const double *x, double *bc,
+                                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

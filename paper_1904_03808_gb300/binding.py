@@ -89,6 +89,8 @@ _SIGS = {
     "mg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_long),
                                   C.POINTER(C.c_long)]),
     "mg_launch_count": (C.c_long, []),
+    "mg_residual_restrict_static": (C.c_int, [C.POINTER(mg_grid), C.POINTER(mg_moduli), _P, _P,
+                                              _P, _P]),
 }
 
 

@@ -34,6 +34,13 @@ constexpr int kProfSlots = 64;
 
 std::atomic<long> qsmg::g_launches{0};
 
+void qsmg::set_last_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
 struct mg_ctx {
     int nlev;
     Dims L[kMaxLev];

@@ -9,6 +9,9 @@
 
 namespace qsmg {
 
+// message for mg_last_error() of the calling thread
+void set_last_error(const char *fmt, ...);
+
 // kernels launched by this library (read through mg_launch_count)
 extern std::atomic<long> g_launches;
 inline void count_launch(long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
