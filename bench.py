@@ -33,7 +33,7 @@ METRIC = ("sec per multigrid solve (rel resid 1e-10) at 256³, mixed vs FP64; "
 UNIT = "s/solve"
 TOL = 1e-10
 PRELOAD = 1.2e9       # Pa, uniform sigma_xz at t0: keeps the STZ rate active
-INNER = 4             # FP32 V-cycles per refinement step
+INNER = 0             # FP32 V-cycles per refinement step (0: chosen per step)
 SMOOTH_BYTES = 36     # algorithmic bytes per node per FP32 sweep: read v, b; write v (9 floats)
 
 

@@ -53,6 +53,8 @@ typedef enum {
 } mg_status;
 
 enum { MG_FP64 = 0, MG_MIXED = 1 };
+/* mg_opts.flags */
+enum { MG_FLAG_COLOUR_PASSES = 1 /* FP32 finest level: one launch per colour */ };
 enum { MG_HIST = 128 };
 
 /* Grid: nx, ny even and >= 4, nz even and >= 2 (cells); h spacing (m). */
@@ -91,13 +93,19 @@ typedef struct {
  *                 coarsest solve).
  *   nu1, nu2      pre/post Gauss-Seidel sweeps (section 3.6 uses 2 and 2).
  *   max_cycles    cap on V-cycles per solve (<= MG_HIST - 1).
- *   inner_cycles  MG_MIXED: FP32 V-cycles per outer refinement step.
+ *   inner_cycles  MG_MIXED: FP32 V-cycles per outer refinement step; 0 picks
+ *                 the count per step from the FP64 residual and the observed
+ *                 V-cycle contraction (at most 10).
+ *   flags         0, or MG_FLAG_COLOUR_PASSES to run the FP32 finest-level
+ *                 sweeps as eight colour launches instead of the tiled
+ *                 two-phase kernel (same arithmetic; kept for comparison).
  */
 typedef struct {
     int precision;
     int nu1, nu2;
     int max_cycles;
     int inner_cycles;
+    int flags;
 } mg_opts;
 
 /* Per-solve statistics.  resid_hist[0] is the relative residual of the

@@ -19,6 +19,7 @@ _lib = None
 MG_OK, MG_ERR_ARG, MG_ERR_SHAPE, MG_ERR_CUDA, MG_ERR_OOM, MG_ERR_NOCONV, MG_ERR_NONFINITE, \
     MG_ERR_STATE = range(8)
 MG_FP64, MG_MIXED = 0, 1
+MG_FLAG_COLOUR_PASSES = 1
 MG_HIST = 128
 
 
@@ -42,7 +43,7 @@ class stz_params(C.Structure):
 
 class mg_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
-                ("max_cycles", C.c_int), ("inner_cycles", C.c_int)]
+                ("max_cycles", C.c_int), ("inner_cycles", C.c_int), ("flags", C.c_int)]
 
 
 class mg_stats(C.Structure):
@@ -145,13 +146,13 @@ class Context:
     """Owns one mg_ctx: a multigrid hierarchy for an nx*ny*nz-cell grid."""
 
     def __init__(self, nx, ny, nz, h, K, mu, bc=None, stz=None, precision=MG_FP64, nu1=2, nu2=2,
-                 max_cycles=100, inner_cycles=4, stream=None):
+                 max_cycles=100, inner_cycles=0, flags=0, stream=None):
         import torch
         L = lib()
         self.shape = (nx, ny, nz)
         g = mg_grid(nx, ny, nz, h)
         m = mg_moduli(K, mu)
-        o = mg_opts(precision, nu1, nu2, max_cycles, inner_cycles)
+        o = mg_opts(precision, nu1, nu2, max_cycles, inner_cycles, flags)
         b = mg_bc(**bc) if isinstance(bc, dict) else bc
         z = stz_params(**stz) if isinstance(stz, dict) else stz
         if stream is None:

@@ -96,16 +96,26 @@ __device__ __forceinline__ void coarse_off(const T *x, const Dims &d, int i, int
     o[2] = s2;
 }
 
-// node of colour `colour` number t (t < (nx/2)(ny/2)nk)
-__device__ __forceinline__ void colour_node(long t, int colour, int hx, int hy, int &i, int &j,
-                                            int &k) {
-    const int ix = (int)(t % hx);
-    const long q = t / hx;
-    const int jy = (int)(q % hy);
-    const int kz = (int)(q / hy);
+// launch shape of the node kernels: 32 x 8 threads over (i, j), grid.z over
+// planes, so no thread divides a flat index
+constexpr int BX = 32, BY = 8;
+
+// node of colour `colour` handled by this thread (false if outside)
+__device__ __forceinline__ bool colour_node(int colour, int hx, int hy, int &i, int &j, int &k) {
+    const int ix = blockIdx.x * BX + threadIdx.x, jy = blockIdx.y * BY + threadIdx.y;
+    if (ix >= hx || jy >= hy) return false;
     i = 2 * ix + (colour & 1);
     j = 2 * jy + ((colour >> 1) & 1);
-    k = 2 * kz + ((colour & 4) ? 1 : 2);
+    k = 2 * (int)blockIdx.z + ((colour & 4) ? 1 : 2);
+    return true;
+}
+
+// interior node (i, j, k), k in 1..nz-1, handled by this thread
+__device__ __forceinline__ bool node_ijk(const Dims &d, int &i, int &j, int &k) {
+    i = blockIdx.x * BX + threadIdx.x;
+    j = blockIdx.y * BY + threadIdx.y;
+    k = blockIdx.z + 1;
+    return i < d.nx && j < d.ny;
 }
 
 // planes of one k-parity among the interior planes 1..nz-1
@@ -113,11 +123,9 @@ inline int colour_planes(int nz, int colour) { return (colour & 4) ? nz / 2 : nz
 
 template <typename T>
 __global__ void k_gs_fine(Dims d, Fine<T> f, const T *__restrict__ b, T *x, int colour, int hx,
-                          int hy, long tot) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
+                          int hy) {
     int i, j, k;
-    colour_node(t, colour, hx, hy, i, j, k);
+    if (!colour_node(colour, hx, hy, i, j, k)) return;
     T o[3];
     fine_off<T, false>(x, d, i, j, k, f.lp, f.kq, o);
     const long p = ((long)k * d.ny + j) * d.nx + i;
@@ -131,11 +139,9 @@ __global__ void k_gs_fine(Dims d, Fine<T> f, const T *__restrict__ b, T *x, int 
 
 template <typename T>
 __global__ void k_gs_coarse(Dims d, Coarse<T> c, const T *__restrict__ b, T *x, int colour, int hx,
-                            int hy, long tot) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
+                            int hy) {
     int i, j, k;
-    colour_node(t, colour, hx, hy, i, j, k);
+    if (!colour_node(colour, hx, hy, i, j, k)) return;
     T o[3];
     coarse_off<T>(x, d, i, j, k, c, o);
     const long p = ((long)k * d.ny + j) * d.nx + i;
@@ -145,21 +151,11 @@ __global__ void k_gs_coarse(Dims d, Coarse<T> c, const T *__restrict__ b, T *x, 
     x[p + 2 * d.cs] = c.Dinv[6] * f0 + c.Dinv[7] * f1 + c.Dinv[8] * f2;
 }
 
-// interior node number t -> (i, j, k), k in 1..nz-1
-__device__ __forceinline__ void interior_node(long t, const Dims &d, int &i, int &j, int &k) {
-    i = (int)(t % d.nx);
-    const long q = t / d.nx;
-    j = (int)(q % d.ny);
-    k = (int)(q / d.ny) + 1;
-}
-
 template <typename T>
 __global__ void k_res_fine(Dims d, Fine<T> f, const T *__restrict__ b, const T *__restrict__ x,
-                           T *__restrict__ r, long tot) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
+                           T *__restrict__ r) {
     int i, j, k;
-    interior_node(t, d, i, j, k);
+    if (!node_ijk(d, i, j, k)) return;
     T o[3];
     fine_off<T, false>(x, d, i, j, k, f.lp, f.kq, o);
     const long p = ((long)k * d.ny + j) * d.nx + i;
@@ -169,11 +165,9 @@ __global__ void k_res_fine(Dims d, Fine<T> f, const T *__restrict__ b, const T *
 
 template <typename T>
 __global__ void k_res_coarse(Dims d, Coarse<T> c, const T *__restrict__ b,
-                             const T *__restrict__ x, T *__restrict__ r, long tot) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
+                             const T *__restrict__ x, T *__restrict__ r) {
     int i, j, k;
-    interior_node(t, d, i, j, k);
+    if (!node_ijk(d, i, j, k)) return;
     T o[3];
     coarse_off<T>(x, d, i, j, k, c, o);
     const long p = ((long)k * d.ny + j) * d.nx + i;
@@ -208,21 +202,35 @@ template <bool WO>
 __global__ void __launch_bounds__(kRedThreads)
     k_res_norm_fine64(Dims d, Fine<double> f, const double *__restrict__ b,
                       const double *__restrict__ x, float *__restrict__ r32, double out_scale,
-                      double *__restrict__ partials, long tot) {
+                      double *__restrict__ partials) {
+    // rows (j, k) are dealt to blocks in a fixed order, columns to threads,
+    // so the partial sums do not depend on timing
     double acc = 0.0;
-    const long stride = (long)gridDim.x * blockDim.x;
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += stride) {
-        int i, j, k;
-        interior_node(t, d, i, j, k);
-        double o[3];
-        fine_off<double, WO>(x, d, i, j, k, f.lp, f.kq, o);
-        const long p = ((long)k * d.ny + j) * d.nx + i;
+    const int nrows = d.ny * (d.nz - 1);
+    for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const int k = row / d.ny + 1, j = row - (k - 1) * d.ny;
+        if (WO && k != 1 && k != d.nz - 1) {
+            // away from the walls the lifted right-hand side is b itself
+            const long p0 = ((long)k * d.ny + j) * d.nx;
+            for (int i = threadIdx.x; i < d.nx; i += blockDim.x)
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const double xc = WO ? 0.0 : x[p + a * d.cs];
-            const double r = b[p + a * d.cs] - (f.d0 * xc + o[a]);
-            acc += r * r;
-            if (r32) r32[p + a * d.cs] = (float)(r * out_scale);
+                for (int a = 0; a < 3; a++) {
+                    const double r = b[p0 + i + a * d.cs];
+                    acc += r * r;
+                }
+            continue;
+        }
+        for (int i = threadIdx.x; i < d.nx; i += blockDim.x) {
+            double o[3];
+            fine_off<double, WO>(x, d, i, j, k, f.lp, f.kq, o);
+            const long p = ((long)k * d.ny + j) * d.nx + i;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const double xc = WO ? 0.0 : x[p + a * d.cs];
+                const double r = b[p + a * d.cs] - (f.d0 * xc + o[a]);
+                acc += r * r;
+                if (r32) r32[p + a * d.cs] = (float)(r * out_scale);
+            }
         }
     }
     const double s = block_sum(acc);
@@ -230,17 +238,17 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 __global__ void __launch_bounds__(kRedThreads)
-    k_sumsq(Dims d, const double *__restrict__ r, double *__restrict__ partials, long tot) {
+    k_sumsq(Dims d, const double *__restrict__ r, double *__restrict__ partials) {
     double acc = 0.0;
-    const long stride = (long)gridDim.x * blockDim.x;
-    const long plane0 = (long)d.ny * d.nx;
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += stride) {
-        const long p = t + plane0;  // interior nodes of component 0 are contiguous
+    const int nrows = d.ny * (d.nz - 1);
+    for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const long p0 = (long)(row + d.ny) * d.nx;  // interior rows start at plane 1
+        for (int i = threadIdx.x; i < d.nx; i += blockDim.x)
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const double v = r[p + a * d.cs];
-            acc += v * v;
-        }
+            for (int a = 0; a < 3; a++) {
+                const double v = r[p0 + i + a * d.cs];
+                acc += v * v;
+            }
     }
     const double s = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -257,11 +265,9 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double *__restrict_
 // restriction R = T^T (full weighting, weights 1, 1/2, 1/4, 1/8 by the
 // number of odd offsets), coarse interior nodes
 template <typename T>
-__global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restrict__ bc, long tot) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
+__global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restrict__ bc) {
     int I, J, K;
-    interior_node(t, c, I, J, K);
+    if (!node_ijk(c, I, J, K)) return;
     T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
     for (int ez = -1; ez <= 1; ez++) {
@@ -294,11 +300,9 @@ __global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restric
 // prolongation x += T xc: fine node 2I is coarse node I, odd fine nodes take
 // the mean of their two neighbours along each odd axis (coarse walls are 0)
 template <typename T>
-__global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restrict__ x, long tot) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
+__global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restrict__ x) {
     int i, j, k;
-    interior_node(t, f, i, j, k);
+    if (!node_ijk(f, i, j, k)) return;
     const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
     const int I1 = (i & 1) ? ((I0 + 1 < c.nx) ? I0 + 1 : 0) : I0;
     const int J1 = (j & 1) ? ((J0 + 1 < c.ny) ? J0 + 1 : 0) : J0;
@@ -342,32 +346,34 @@ __global__ void k_coarse_solve(Dims d, const double *__restrict__ Ainv, int n,
     }
 }
 
-__global__ void k_zero_interior(Dims d, double *__restrict__ x, long tot) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
-    const long plane0 = (long)d.ny * d.nx;
+__global__ void k_zero_interior(Dims d, double *__restrict__ x) {
+    int i, j, k;
+    if (!node_ijk(d, i, j, k)) return;
+    const long p = ((long)k * d.ny + j) * d.nx + i;
 #pragma unroll
-    for (int a = 0; a < 3; a++) x[a * d.cs + plane0 + t] = 0.0;
+    for (int a = 0; a < 3; a++) x[a * d.cs + p] = 0.0;
 }
 
 __global__ void k_axpy_f32(Dims d, double scale, const float *__restrict__ e,
-                           double *__restrict__ v, long tot) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
-    const long p = (long)d.ny * d.nx + t;
+                           double *__restrict__ v) {
+    int i, j, k;
+    if (!node_ijk(d, i, j, k)) return;
+    const long p = ((long)k * d.ny + j) * d.nx + i;
 #pragma unroll
     for (int a = 0; a < 3; a++) v[a * d.cs + p] += scale * (double)e[a * d.cs + p];
 }
 
-inline long interior_nodes(const Dims &d) { return (long)d.nx * d.ny * (d.nz - 1); }
+inline dim3 node_grid(int nx, int ny, int nplanes) {
+    return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nplanes);
+}
+const dim3 kBlock(BX, BY);
 
 template <typename T>
 cudaError_t gs_fine_t(const Dims &d, const Fine<T> &f, const T *b, T *x, int colour,
                       cudaStream_t s) {
     const int hx = d.nx / 2, hy = d.ny / 2, nk = colour_planes(d.nz, colour);
-    const long tot = (long)hx * hy * nk;
-    if (tot <= 0) return cudaSuccess;
-    k_gs_fine<T><<<nblocks(tot), kThreads, 0, s>>>(d, f, b, x, colour, hx, hy, tot);
+    if (nk <= 0) return cudaSuccess;
+    k_gs_fine<T><<<node_grid(hx, hy, nk), kBlock, 0, s>>>(d, f, b, x, colour, hx, hy);
     count_launch();
     return cudaGetLastError();
 }
@@ -376,9 +382,8 @@ template <typename T>
 cudaError_t gs_coarse_t(const Dims &d, const Coarse<T> &c, const T *b, T *x, int colour,
                         cudaStream_t s) {
     const int hx = d.nx / 2, hy = d.ny / 2, nk = colour_planes(d.nz, colour);
-    const long tot = (long)hx * hy * nk;
-    if (tot <= 0) return cudaSuccess;
-    k_gs_coarse<T><<<nblocks(tot), kThreads, 0, s>>>(d, c, b, x, colour, hx, hy, tot);
+    if (nk <= 0) return cudaSuccess;
+    k_gs_coarse<T><<<node_grid(hx, hy, nk), kBlock, 0, s>>>(d, c, b, x, colour, hx, hy);
     count_launch();
     return cudaGetLastError();
 }
@@ -405,8 +410,7 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float 
 template <typename T>
 static cudaError_t res_fine_t(const Dims &d, const Fine<T> &f, const T *b, const T *x, T *r,
                               cudaStream_t s) {
-    const long tot = interior_nodes(d);
-    k_res_fine<T><<<nblocks(tot), kThreads, 0, s>>>(d, f, b, x, r, tot);
+    k_res_fine<T><<<node_grid(d.nx, d.ny, d.nz - 1), kBlock, 0, s>>>(d, f, b, x, r);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -424,8 +428,7 @@ static cudaError_t res_fine_t(const Dims &d, const Fine<T> &f, const T *b, const
 template <typename T>
 static cudaError_t res_coarse_t(const Dims &d, const Coarse<T> &c, const T *b, const T *x, T *r,
                                 cudaStream_t s) {
-    const long tot = interior_nodes(d);
-    k_res_coarse<T><<<nblocks(tot), kThreads, 0, s>>>(d, c, b, x, r, tot);
+    k_res_coarse<T><<<node_grid(d.nx, d.ny, d.nz - 1), kBlock, 0, s>>>(d, c, b, x, r);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -459,19 +462,18 @@ cudaError_t residual_coarse(const Dims &d, const Coarse<float> &c, const float *
 cudaError_t residual_norm_fine64(const Dims &d, const Fine<double> &f, const double *b,
                                  const double *x, bool wall_only, float *r32, double out_scale,
                                  double *partials, cudaStream_t s) {
-    const long tot = interior_nodes(d);
     if (wall_only)
         k_res_norm_fine64<true><<<kRedBlocks, kRedThreads, 0, s>>>(d, f, b, x, r32, out_scale,
-                                                                   partials, tot);
+                                                                   partials);
     else
         k_res_norm_fine64<false><<<kRedBlocks, kRedThreads, 0, s>>>(d, f, b, x, r32, out_scale,
-                                                                    partials, tot);
+                                                                    partials);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t sumsq(const Dims &d, const double *r, double *partials, cudaStream_t s) {
-    k_sumsq<<<kRedBlocks, kRedThreads, 0, s>>>(d, r, partials, interior_nodes(d));
+    k_sumsq<<<kRedBlocks, kRedThreads, 0, s>>>(d, r, partials);
     count_launch();
     return cudaGetLastError();
 }
@@ -485,8 +487,8 @@ cudaError_t sum_partials(const double *partials, double *out, cudaStream_t s) {
 template <typename T>
 static cudaError_t restrict_t(const Dims &f, const T *r, T *bc, cudaStream_t s) {
     const Dims c = make_dims(f.nx / 2, f.ny / 2, f.nz / 2);
-    const long tot = interior_nodes(c);
-    if (tot > 0) k_restrict<T><<<nblocks(tot), kThreads, 0, s>>>(f, c, r, bc, tot);
+    if (c.nz < 2) return cudaSuccess;
+    k_restrict<T><<<node_grid(c.nx, c.ny, c.nz - 1), kBlock, 0, s>>>(f, c, r, bc);
     count_launch();
     return cudaGetLastError();
 }
@@ -500,8 +502,7 @@ cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_
 template <typename T>
 static cudaError_t prolong_t(const Dims &f, const T *xc, T *x, cudaStream_t s) {
     const Dims c = make_dims(f.nx / 2, f.ny / 2, f.nz / 2);
-    const long tot = interior_nodes(f);
-    k_prolong<T><<<nblocks(tot), kThreads, 0, s>>>(f, c, xc, x, tot);
+    k_prolong<T><<<node_grid(f.nx, f.ny, f.nz - 1), kBlock, 0, s>>>(f, c, xc, x);
     count_launch();
     return cudaGetLastError();
 }
@@ -530,15 +531,13 @@ cudaError_t coarse_solve(const Dims &d, const double *Ainv, int n, const float *
 }
 
 cudaError_t zero_interior(const Dims &d, double *x, cudaStream_t s) {
-    const long tot = interior_nodes(d);
-    k_zero_interior<<<nblocks(tot), kThreads, 0, s>>>(d, x, tot);
+    k_zero_interior<<<node_grid(d.nx, d.ny, d.nz - 1), kBlock, 0, s>>>(d, x);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t axpy_f32(const Dims &d, double scale, const float *e, double *v, cudaStream_t s) {
-    const long tot = interior_nodes(d);
-    k_axpy_f32<<<nblocks(tot), kThreads, 0, s>>>(d, scale, e, v, tot);
+    k_axpy_f32<<<node_grid(d.nx, d.ny, d.nz - 1), kBlock, 0, s>>>(d, scale, e, v);
     count_launch();
     return cudaGetLastError();
 }

@@ -59,6 +59,7 @@ struct mg_ctx {
     // device buffers (level 0 x/b in FP64 mode are the caller's arrays)
     double *x64[kMaxLev], *b64[kMaxLev], *r64[kMaxLev];
     float *x32[kMaxLev], *b32[kMaxLev], *r32[kMaxLev];
+    float *xs32[kMaxLev];  // ping-pong partners of the tiled FP32 sweeps
     double *Ainv;
     int ncoarse;
     double *partials, *dsum, *hsum;
@@ -324,20 +325,76 @@ mg_status gs_pass(mg_ctx *ctx, int l, const T *b, T *x, int colour) {
     return MG_OK;
 }
 
+// FP32 sweeps on level l with the tiled two-phase kernels, ping-ponging
+// between x and the level's partner buffer (whose wall planes are made equal
+// to x's; the solver's own level arrays and partners all keep zero walls)
+mg_status sweeps_tiled(mg_ctx *ctx, int l, const float *b, float *x, int sweeps, bool descending) {
+    const Dims &d = ctx->L[l];
+    float *a = x, *o = ctx->xs32[l];
+    if (x != ctx->x32[l]) {
+        const size_t plane = (size_t)d.ny * d.nx;
+        for (int c = 0; c < 3; c++) {
+            CK(cudaMemcpyAsync(o + c * d.cs, x + c * d.cs, plane * sizeof(float),
+                               cudaMemcpyDeviceToDevice, ctx->st));
+            CK(cudaMemcpyAsync(o + c * d.cs + d.nz * plane, x + c * d.cs + d.nz * plane,
+                               plane * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+        }
+    }
+    for (int s = 0; s < sweeps; s++) {
+        if (l == 0)
+            CK(gs_sweep_fine_tiled(d, ctx->f32, b, a, o, descending, ctx->st));
+        else
+            CK(gs_sweep_coarse_tiled(d, ctx->c32[l], b, a, o, descending, ctx->st));
+        float *t = a;
+        a = o;
+        o = t;
+    }
+    if (a != x)
+        CK(cudaMemcpyAsync(x, a, 3 * (size_t)d.cs * sizeof(float), cudaMemcpyDeviceToDevice,
+                           ctx->st));
+    if (x != ctx->x32[l]) {
+        // the partner holds x's walls; restore the solver's zero walls
+        const size_t plane = (size_t)d.ny * d.nx;
+        for (int c = 0; c < 3; c++) {
+            CK(cudaMemsetAsync(ctx->xs32[l] + c * d.cs, 0, plane * sizeof(float), ctx->st));
+            CK(cudaMemsetAsync(ctx->xs32[l] + c * d.cs + d.nz * plane, 0, plane * sizeof(float),
+                               ctx->st));
+        }
+    }
+    return MG_OK;
+}
+
 template <typename T>
-mg_status smooth(mg_ctx *ctx, int l, const T *b, T *x, int sweeps, bool descending) {
-    const bool timed = ctx->prof_on && l == 0 && sweeps > 0;
+mg_status sweeps_colour(mg_ctx *ctx, int l, const T *b, T *x, int sweeps, bool descending) {
+    for (int s = 0; s < sweeps; s++)
+        for (int c = 0; c < 8; c++) CKS(gs_pass<T>(ctx, l, b, x, descending ? 7 - c : c));
+    return MG_OK;
+}
+
+template <typename T>
+mg_status sweeps(mg_ctx *ctx, int l, const T *b, T *x, int n, bool descending) {
+    return sweeps_colour<T>(ctx, l, b, x, n, descending);
+}
+
+template <>
+mg_status sweeps<float>(mg_ctx *ctx, int l, const float *b, float *x, int n, bool descending) {
+    if (!(ctx->opts.flags & MG_FLAG_COLOUR_PASSES)) return sweeps_tiled(ctx, l, b, x, n, descending);
+    return sweeps_colour<float>(ctx, l, b, x, n, descending);
+}
+
+template <typename T>
+mg_status smooth(mg_ctx *ctx, int l, const T *b, T *x, int sweeps_n, bool descending) {
+    const bool timed = ctx->prof_on && l == 0 && sweeps_n > 0;
     if (timed && ctx->npend == kProfSlots) {
         CK(cudaStreamSynchronize(ctx->st));
         CKS(prof_drain(ctx));
     }
     const long launches0 = g_launches.load();
     if (timed) CK(cudaEventRecord(ctx->ev[ctx->npend][0], ctx->st));
-    for (int s = 0; s < sweeps; s++)
-        for (int c = 0; c < 8; c++) CKS(gs_pass<T>(ctx, l, b, x, descending ? 7 - c : c));
+    CKS(sweeps<T>(ctx, l, b, x, sweeps_n, descending));
     if (timed) {
         CK(cudaEventRecord(ctx->ev[ctx->npend][1], ctx->st));
-        ctx->pend_sweeps[ctx->npend] = sweeps;
+        ctx->pend_sweeps[ctx->npend] = sweeps_n;
         ctx->pend_launches[ctx->npend] = g_launches.load() - launches0;
         ctx->npend++;
     }
@@ -423,8 +480,22 @@ mg_status solve_fp64(mg_ctx *ctx, const double *b, double *v, double tol, mg_sta
 }
 
 // FP32 V-cycles on the correction equation inside FP64 iterative refinement:
-//   r = b - A v (FP64, stored as float(r / s)), e ~ A^{-1} r by
-//   inner_cycles FP32 V-cycles from e = 0, v += s e.
+//   r = b - A v (FP64, stored as float(r / s)), e ~ A^{-1} r by FP32 V-cycles
+//   from e = 0, v += s e.
+// With opts.inner_cycles > 0 every refinement step runs that many cycles.
+// With 0 the count is chosen per step: enough cycles to bring the FP64
+// residual to tol at the contraction factor observed so far (initially 0.4),
+// at least 1 and at most kMaxInner, so that few FP64 residuals are needed.
+constexpr int kMaxInner = 10;
+
+int inner_count(const mg_ctx *ctx, double rel, double tol, double kappa) {
+    if (ctx->opts.inner_cycles > 0) return ctx->opts.inner_cycles;
+    if (!(tol > 0.0) || !(rel > tol)) return kMaxInner;
+    const double need = log(0.7 * tol / rel) / log(kappa);
+    int n = (int)ceil(need);
+    return n < 1 ? 1 : (n > kMaxInner ? kMaxInner : n);
+}
+
 mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_stats *st) {
     double bn, rn;
     CKS(fine_resnorm(ctx, b, v, true, nullptr, 0.0, &bn));
@@ -440,6 +511,7 @@ mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_st
     double rel = rn / bn;
     st->resid_hist[0] = rel;
     int outer = 0, cycles = 0;
+    double kappa = 0.4;  // V-cycle contraction estimate, refined from the history
     const size_t n0 = corner_count(ctx->L[0]);
     for (;;) {
         st->rel_resid = rel;
@@ -458,15 +530,20 @@ mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_st
             }
             return MG_OK;
         }
+        const int n = inner_count(ctx, rel, tol, kappa);
         CK(cudaMemsetAsync(ctx->x32[0], 0, n0 * sizeof(float), ctx->st));
-        for (int c = 0; c < ctx->opts.inner_cycles; c++)
-            CKS(vcycle<float>(ctx, 0, ctx->b32[0], ctx->x32[0]));
+        for (int c = 0; c < n; c++) CKS(vcycle<float>(ctx, 0, ctx->b32[0], ctx->x32[0]));
         CK(axpy_f32(ctx->L[0], scale, ctx->x32[0], v, ctx->st));
         outer++;
-        cycles += ctx->opts.inner_cycles;
+        cycles += n;
         scale = rn;
         CKS(fine_resnorm(ctx, b, v, false, ctx->b32[0], 1.0 / scale, &rn));
-        rel = rn / bn;
+        const double rel_new = rn / bn;
+        if (rel_new > 0.0 && rel_new < rel) {
+            const double k = pow(rel_new / rel, 1.0 / n);
+            kappa = k < 0.05 ? 0.05 : (k > 0.9 ? 0.9 : k);
+        }
+        rel = rel_new;
         if (outer < MG_HIST) st->resid_hist[outer] = rel;
     }
 }
@@ -569,7 +646,7 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         return MG_ERR_ARG;
     }
     if (opts->nu1 < 0 || opts->nu2 < 0 || opts->max_cycles < 0 || opts->max_cycles >= MG_HIST ||
-        (opts->precision == MG_MIXED && opts->inner_cycles < 1)) {
+        opts->inner_cycles < 0) {
         set_err("mg_setup: bad nu1/nu2/max_cycles/inner_cycles");
         return MG_ERR_ARG;
     }
@@ -654,6 +731,7 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         ALLOC(ctx->x32[l], n);
         ALLOC(ctx->b32[l], n);
         ALLOC(ctx->r32[l], n);
+        ALLOC(ctx->xs32[l], n);
     }
     ALLOC(ctx->Ainv, Ainv.size());
     ALLOC(ctx->partials, (size_t)kRedBlocks);

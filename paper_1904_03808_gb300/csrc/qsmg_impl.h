@@ -64,6 +64,14 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<double> &c, const doubl
 cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float *b, float *x,
                              int colour, cudaStream_t s);
 
+// tiled FP32 finest-level sweep vin -> vout (two phase launches)
+cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,
+                                const float *vin, float *vout, bool descending, cudaStream_t s);
+
+// tiled FP32 coarse-level sweep vin -> vout (27-point block stencil)
+cudaError_t gs_sweep_coarse_tiled(const Dims &d, const Coarse<float> &c, const float *b,
+                                  const float *vin, float *vout, bool descending, cudaStream_t s);
+
 // r = b - A x (interior), r walls zero
 cudaError_t residual_fine(const Dims &d, const Fine<double> &f, const double *b, const double *x,
                           double *r, cudaStream_t s);

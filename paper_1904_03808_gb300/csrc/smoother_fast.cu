@@ -1,0 +1,295 @@
+// smoother_fast.cu -- tiled two-phase Gauss-Seidel sweeps (any level).
+//
+// One 8-colour sweep (colours (i&1)+2(j&1)+4(k&1), visited 0..7, or 7..0)
+// in two launches.  Colours 0-3 live on the even-k planes and 4-7 on the
+// odd-k planes, and the stencil couples a plane only to its two neighbours,
+// so:
+//   phase 1 updates every plane of the first k-parity (its 4 in-plane colours
+//           in order), reading its z-neighbours' old values;
+//   phase 2 updates every plane of the other parity, reading the new values
+//           phase 1 wrote.
+// This is the same computation as eight colour passes (every node sees the
+// same neighbour values), with v read and written about twice per sweep
+// instead of eight times.
+//
+// Inside one plane a CTA owns a TX x TY tile and stages a window of that plane
+// with a halo of HX columns and HY rows in shared memory (17 KB in FP32, so 8
+// CTAs fit on an SM); the z-neighbour planes and the right-hand side, which
+// the phase only reads, come through the read-only cache.  The same kernel
+// serves the finest level (structured 19-point operator) and the coarse
+// levels (Galerkin 27-point block stencil); both couple a node only to the 8
+// in-plane neighbours and to 9 nodes in each adjacent plane.  The 4 in-plane colours are
+// computed on shrinking regions so that the tile's own nodes see exactly the
+// neighbour values of the sequential order (the halo nodes are recomputed,
+// identically, by the neighbouring CTAs).  The sweep is out of place (vin ->
+// vout) so no CTA ever reads a value another CTA has already overwritten;
+// vout's wall planes must hold the wall values.
+#include "qsmg_impl.h"
+
+namespace qsmg {
+namespace {
+
+constexpr int TX = 64, TY = 16;        // tile owned by one CTA
+constexpr int HX = 4, HY = 2;          // staging halo (x, y)
+constexpr int WX = TX + 2 * HX;        // 72 window columns
+constexpr int WY = TY + 2 * HY;        // 20 window rows
+constexpr int WH = WX / 2;             // words per parity half-row
+constexpr int WIN1 = WY * WX;          // one component of a window
+constexpr int WIN = 3 * WIN1;          // three components
+constexpr int NT = 256;
+
+template <typename T>
+constexpr size_t smem_bytes() {
+    return WIN * sizeof(T) + (WX + WY) * sizeof(int);
+}
+
+// window element (component c, row wy, column wx): columns split by parity so
+// that the 2-strided nodes of one colour sit in consecutive words
+__device__ __forceinline__ int widx(int c, int wy, int wx) {
+    return ((c * WY + wy) * 2 + (wx & 1)) * WH + (wx >> 1);
+}
+
+__device__ __forceinline__ int wrap_mod(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// what one node update sees: the staged plane P (shared memory), the
+// z-neighbour planes L, H and the right-hand side B of this plane (global,
+// read-only), addressed through the wrapped row / column offsets rowg, colg
+template <typename T>
+struct View {
+    T *P;
+    const T *__restrict__ L;
+    const T *__restrict__ H;
+    const T *__restrict__ B;
+    long cs;
+    const int *rowg, *colg;
+};
+
+// finest level: the structured 19-point operator (scaled Eq. 30)
+template <typename T>
+struct FineOp {
+    Fine<T> f;
+    __device__ __forceinline__ void update(const View<T> &v, int wx, int wy) const {
+        T *P = v.P;
+        const long cs = v.cs;
+        const int xm = wx - 1, xp = wx + 1, ym = wy - 1, yp = wy + 1;
+        const int g00 = v.rowg[wy] + v.colg[wx];
+        const int gm0 = v.rowg[wy] + v.colg[xm], gp0 = v.rowg[wy] + v.colg[xp];
+        const int g0m = v.rowg[ym] + v.colg[wx], g0p = v.rowg[yp] + v.colg[wx];
+        const T lp = f.lp, kq = f.kq;
+#define Pv(c, yy, xx) P[widx(c, yy, xx)]
+#define Lg(c, g) __ldg(v.L + (c) * cs + (g))
+#define Hg(c, g) __ldg(v.H + (c) * cs + (g))
+        const T a0 = lp * (Pv(0, wy, xm) + Pv(0, wy, xp)) + (Pv(0, ym, wx) + Pv(0, yp, wx)) +
+                     (Lg(0, g00) + Hg(0, g00));
+        const T a1 = lp * (Pv(1, ym, wx) + Pv(1, yp, wx)) + (Pv(1, wy, xm) + Pv(1, wy, xp)) +
+                     (Lg(1, g00) + Hg(1, g00));
+        const T a2 = lp * (Lg(2, g00) + Hg(2, g00)) + (Pv(2, wy, xm) + Pv(2, wy, xp)) +
+                     (Pv(2, ym, wx) + Pv(2, yp, wx));
+#define MXY(c) (Pv(c, yp, xp) - Pv(c, ym, xp) - Pv(c, yp, xm) + Pv(c, ym, xm))
+#define MXZ(c) (Hg(c, gp0) - Lg(c, gp0) - Hg(c, gm0) + Lg(c, gm0))
+#define MYZ(c) (Hg(c, g0p) - Lg(c, g0p) - Hg(c, g0m) + Lg(c, g0m))
+        const T o0 = -(a0 + kq * (MXY(1) + MXZ(2)));
+        const T o1 = -(a1 + kq * (MXY(0) + MYZ(2)));
+        const T o2 = -(a2 + kq * (MXZ(0) + MYZ(1)));
+        Pv(0, wy, wx) = (__ldg(v.B + g00) - o0) * f.dinv;
+        Pv(1, wy, wx) = (__ldg(v.B + cs + g00) - o1) * f.dinv;
+        Pv(2, wy, wx) = (__ldg(v.B + 2 * cs + g00) - o2) * f.dinv;
+#undef Pv
+#undef Lg
+#undef Hg
+#undef MXY
+#undef MXZ
+#undef MYZ
+    }
+};
+
+// coarse levels: one constant 27-point stencil of 3x3 blocks (Eq. 36)
+template <typename T>
+struct CoarseOp {
+    Coarse<T> c;
+    __device__ __forceinline__ void update(const View<T> &v, int wx, int wy) const {
+        T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int dz = -1; dz <= 1; dz++)
+#pragma unroll
+            for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int dd = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                    if (dd == 13) continue;
+                    T u0, u1, u2;
+                    if (dz == 0) {
+                        u0 = v.P[widx(0, wy + dy, wx + dx)];
+                        u1 = v.P[widx(1, wy + dy, wx + dx)];
+                        u2 = v.P[widx(2, wy + dy, wx + dx)];
+                    } else {
+                        const T *Z = dz < 0 ? v.L : v.H;
+                        const int g = v.rowg[wy + dy] + v.colg[wx + dx];
+                        u0 = __ldg(Z + g);
+                        u1 = __ldg(Z + v.cs + g);
+                        u2 = __ldg(Z + 2 * v.cs + g);
+                    }
+                    const T *S = c.S + dd * 9;
+                    s0 += S[0] * u0 + S[1] * u1 + S[2] * u2;
+                    s1 += S[3] * u0 + S[4] * u1 + S[5] * u2;
+                    s2 += S[6] * u0 + S[7] * u1 + S[8] * u2;
+                }
+        const int g00 = v.rowg[wy] + v.colg[wx];
+        const T f0 = __ldg(v.B + g00) - s0, f1 = __ldg(v.B + v.cs + g00) - s1,
+                f2 = __ldg(v.B + 2 * v.cs + g00) - s2;
+        v.P[widx(0, wy, wx)] = c.Dinv[0] * f0 + c.Dinv[1] * f1 + c.Dinv[2] * f2;
+        v.P[widx(1, wy, wx)] = c.Dinv[3] * f0 + c.Dinv[4] * f1 + c.Dinv[5] * f2;
+        v.P[widx(2, wy, wx)] = c.Dinv[6] * f0 + c.Dinv[7] * f1 + c.Dinv[8] * f2;
+    }
+};
+
+// resident CTAs per SM the register budget is cut for: the 27-point operator
+// keeps its 243 coefficients in registers (~128 registers a thread in FP32),
+// the 19-point one needs about 40
+template <class Op>
+struct MinBlocks {
+    static constexpr int value = 4;
+};
+template <>
+struct MinBlocks<CoarseOp<float>> {
+    static constexpr int value = 2;
+};
+
+// update the nodes of in-plane colour (pi, pj) inside window region
+// [xa, xb) x [ya, yb)
+template <typename T, class Op>
+__device__ __forceinline__ void colour_pass(const View<T> &v, const Op &op, int pi, int pj,
+                                            int xa, int xb, int ya, int yb) {
+    const int ua = (xa - pi + 1) >> 1, ub = (xb - pi + 1) >> 1;
+    const int wa = (ya - pj + 1) >> 1, wb = (yb - pj + 1) >> 1;
+    const int nu = ub - ua, n = nu * (wb - wa);
+    for (int t = threadIdx.x; t < n; t += NT) {
+        const int wx = 2 * (ua + t % nu) + pi;
+        const int wy = 2 * (wa + t / nu) + pj;
+        op.update(v, wx, wy);
+    }
+}
+
+// 2 x T in one aligned load (x0 - HX and nx are even)
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    typedef float2 V;
+};
+template <>
+struct Pair<double> {
+    typedef double2 V;
+};
+
+// phase kernel: plane k = 2 * blockIdx.z + kbase, one TX x TY tile per CTA.
+// F selects the in-plane colour order (F,F), (1-F,F), (F,1-F), (1-F,1-F) in
+// (i, j) parity.  zsrc holds the z-neighbour planes (old values in the first
+// phase, the first phase's output in the second).
+template <typename T, class Op, int F>
+__global__ void __launch_bounds__(NT, MinBlocks<Op>::value)
+    k_gs_tiled(Dims d, Op op, const T *__restrict__ b, const T *__restrict__ vin,
+               const T *__restrict__ zsrc, T *__restrict__ vout, int kbase) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sP = reinterpret_cast<T *>(smem_raw);
+    int *colg = reinterpret_cast<int *>(sP + WIN), *rowg = colg + WX;
+    typedef typename Pair<T>::V V2;
+    const int nx = d.nx, ny = d.ny;
+    const long ps = (long)nx * ny, cs = d.cs;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int k = 2 * blockIdx.z + kbase;
+    for (int e = threadIdx.x; e < WX + WY; e += NT) {
+        if (e < WX) colg[e] = wrap_mod(x0 - HX + e, nx);
+        else rowg[e - WX] = wrap_mod(y0 - HY + (e - WX), ny) * nx;
+    }
+    __syncthreads();
+    // stage the plane's window as (even, odd) column pairs
+    const T *src = vin + (long)k * ps;
+    for (int e = threadIdx.x; e < 3 * WY * WH; e += NT) {
+        const int c = e / (WY * WH), r = e - c * (WY * WH);
+        const int wy = r / WH, h = r - wy * WH;
+        const V2 p2 = __ldg(reinterpret_cast<const V2 *>(src + c * cs + rowg[wy] + colg[2 * h]));
+        sP[widx(c, wy, 2 * h)] = p2.x;
+        sP[widx(c, wy, 2 * h + 1)] = p2.y;
+    }
+    __syncthreads();
+    View<T> v;
+    v.P = sP;
+    v.L = zsrc + (long)(k - 1) * ps;
+    v.H = zsrc + (long)(k + 1) * ps;
+    v.B = b + (long)k * ps;
+    v.cs = cs;
+    v.rowg = rowg;
+    v.colg = colg;
+    // the 4 in-plane colours on shrinking regions (window coordinates; the
+    // tile is [HX, HX+TX) x [HY, HY+TY))
+    colour_pass<T, Op>(v, op, F, F, 1, WX - 1, 1, WY - 1);
+    __syncthreads();
+    colour_pass<T, Op>(v, op, 1 - F, F, 2, WX - 2, 1, WY - 1);
+    __syncthreads();
+    colour_pass<T, Op>(v, op, F, 1 - F, 3, WX - 3, 2, WY - 2);
+    __syncthreads();
+    colour_pass<T, Op>(v, op, 1 - F, 1 - F, 4, WX - 4, 2, WY - 2);
+    __syncthreads();
+    // store the tile (nodes inside the grid only) as pairs
+    T *out = vout + (long)k * ps;
+    for (int e = threadIdx.x; e < 3 * TY * (TX / 2); e += NT) {
+        const int c = e / (TY * (TX / 2)), r = e - c * (TY * (TX / 2));
+        const int ty = r / (TX / 2), h = r - ty * (TX / 2);
+        const int gx = x0 + 2 * h, gy = y0 + ty;
+        if (gx < nx && gy < ny) {
+            V2 p2;
+            p2.x = sP[widx(c, ty + HY, 2 * h + HX)];
+            p2.y = sP[widx(c, ty + HY, 2 * h + HX + 1)];
+            *reinterpret_cast<V2 *>(out + c * cs + (long)gy * nx + gx) = p2;
+        }
+    }
+}
+
+template <typename T, class Op, int F>
+cudaError_t launch_phase(const Dims &d, const Op &op, const T *b, const T *vin, const T *zsrc,
+                         T *vout, int par, cudaStream_t s) {
+    // planes of parity par among the interior planes 1..nz-1
+    const int kbase = par ? 1 : 2;
+    const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
+    if (nplanes <= 0) return cudaSuccess;
+    constexpr size_t smem = smem_bytes<T>();
+    dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, nplanes);
+    k_gs_tiled<T, Op, F><<<grid, NT, smem, s>>>(d, op, b, vin, zsrc, vout, kbase);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, class Op>
+cudaError_t sweep(const Dims &d, const Op &op, const T *b, const T *vin, T *vout,
+                  bool descending, cudaStream_t s) {
+    cudaError_t e;
+    if (!descending) {
+        e = launch_phase<T, Op, 0>(d, op, b, vin, vin, vout, 0, s);  // colours 0-3, even planes
+        if (e != cudaSuccess) return e;
+        return launch_phase<T, Op, 0>(d, op, b, vin, vout, vout, 1, s);  // colours 4-7, odd planes
+    }
+    e = launch_phase<T, Op, 1>(d, op, b, vin, vin, vout, 1, s);  // colours 7-4, odd planes
+    if (e != cudaSuccess) return e;
+    return launch_phase<T, Op, 1>(d, op, b, vin, vout, vout, 0, s);  // colours 3-0, even planes
+}
+
+}  // namespace
+
+// one 8-colour sweep vin -> vout (vout's wall planes must hold the walls)
+cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,
+                                const float *vin, float *vout, bool descending, cudaStream_t s) {
+    FineOp<float> op{f};
+    return sweep<float>(d, op, b, vin, vout, descending, s);
+}
+
+cudaError_t gs_sweep_coarse_tiled(const Dims &d, const Coarse<float> &c, const float *b,
+                                  const float *vin, float *vout, bool descending, cudaStream_t s) {
+    CoarseOp<float> op{c};
+    return sweep<float>(d, op, b, vin, vout, descending, s);
+}
+
+}  // namespace qsmg

@@ -9,8 +9,19 @@
 namespace qsmg {
 namespace {
 
-constexpr int kThreads = 256;
-inline unsigned nblocks(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+// 32 x 8 threads over (i, j), grid.z over planes: no flat-index division
+constexpr int BX = 32, BY = 8;
+const dim3 kBlock(BX, BY);
+inline dim3 cell_grid(int nx, int ny, int nplanes) {
+    return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nplanes);
+}
+
+__device__ __forceinline__ bool cell_ijk(int nx, int ny, int &i, int &j, int &k) {
+    i = blockIdx.x * BX + threadIdx.x;
+    j = blockIdx.y * BY + threadIdx.y;
+    k = blockIdx.z;
+    return i < nx && j < ny;
+}
 
 struct StzConst {
     double eDT_over_tau0;  // exp(-Delta/(kB T)) / tau0
@@ -69,11 +80,9 @@ __global__ void k_stress_predict(StepParams p, StzConst c, const double *__restr
                                  const double *__restrict__ sig, const double *__restrict__ chi,
                                  double *__restrict__ sig_star, double *__restrict__ dpl,
                                  double *__restrict__ sbar_out, long nc) {
-    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nc) return;
-    const int i = (int)(q % p.nx);
-    const long r = q / p.nx;
-    const int j = (int)(r % p.ny), k = (int)(r / p.ny);
+    int i, j, k;
+    if (!cell_ijk(p.nx, p.ny, i, j, k)) return;
+    const long q = ((long)k * p.ny + j) * p.nx + i;
     double G[3][3];
     cell_gradient(v, p.nx, p.ny, p.nz, 0.25 / p.h, i, j, k, G);
     double s6[6];
@@ -109,12 +118,10 @@ __global__ void k_chi_update(StepParams p, StzConst c, const double *__restrict_
                              const double *__restrict__ chi, const double *__restrict__ dpl,
                              const double *__restrict__ sbar, double *__restrict__ chi_new,
                              long nc) {
-    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nc) return;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int i = (int)(q % nx);
-    const long r = q / nx;
-    const int j = (int)(r % ny), k = (int)(r / ny);
+    int i, j, k;
+    if (!cell_ijk(nx, ny, i, j, k)) return;
+    const long q = ((long)k * ny + j) * nx + i;
     const long pl = (long)nx * ny;
     const int ip = (i + 1 < nx) ? i + 1 : 0, im = i ? i - 1 : nx - 1;
     const int jp = (j + 1 < ny) ? j + 1 : 0, jm = j ? j - 1 : ny - 1;
@@ -151,13 +158,11 @@ __global__ void k_chi_update(StepParams p, StzConst c, const double *__restrict_
 // b = (h^2/(mu dt)) div sigma* at interior corners; the corner derivative is
 // Eq. (31) shifted by half a cell: cells (i-1..i, j-1..j, k-1..k)
 __global__ void k_div_rhs(StepParams p, const double *__restrict__ ss, double *__restrict__ b,
-                          long tot, double scale) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot) return;
+                          double scale) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int i = (int)(t % nx);
-    const long r = t / nx;
-    const int j = (int)(r % ny), k = (int)(r / ny) + 1;
+    int i, j, k;
+    if (!cell_ijk(nx, ny, i, j, k)) return;
+    k += 1;  // interior corner planes 1..nz-1
     const int im = i ? i - 1 : nx - 1, jm = j ? j - 1 : ny - 1;
     const long nc = (long)nx * ny * nz, pl = (long)nx * ny;
     // the 8 surrounding cells c[dk][dj][di], d = 0 is the lower neighbour
@@ -191,11 +196,9 @@ __global__ void k_stress_correct(StepParams p, const double *__restrict__ v,
                                  const double *__restrict__ ss, double *__restrict__ sig,
                                  const double *__restrict__ chi_src, double *__restrict__ chi_dst,
                                  long nc) {
-    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nc) return;
-    const int i = (int)(q % p.nx);
-    const long r = q / p.nx;
-    const int j = (int)(r % p.ny), k = (int)(r / p.ny);
+    int i, j, k;
+    if (!cell_ijk(p.nx, p.ny, i, j, k)) return;
+    const long q = ((long)k * p.ny + j) * p.nx + i;
     double G[3][3];
     cell_gradient(v, p.nx, p.ny, p.nz, 0.25 / p.h, i, j, k, G);
     const double tr = G[0][0] + G[1][1] + G[2][2];
@@ -211,10 +214,10 @@ __global__ void k_stress_correct(StepParams p, const double *__restrict__ v,
 
 // wall velocities of section 4 (simple shear with ramp) and section 5 (disc)
 __global__ void k_wall_fill(WallParams w, double *__restrict__ v) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= w.nx || j >= w.ny) return;
     const long pl = (long)w.nx * w.ny;
-    if (t >= pl) return;
-    const int i = (int)(t % w.nx), j = (int)(t / w.nx);
+    const long t = (long)j * w.nx + i;
     double top[3] = {0.0, 0.0, 0.0}, bot[3] = {0.0, 0.0, 0.0};
     if (w.kind == 0) {
         const double U = (w.t < w.t_ramp) ? w.U_B * w.t / w.t_ramp : w.U_B;
@@ -245,8 +248,8 @@ cudaError_t stress_predict(const StepParams &p, const double *v, const double *s
                            const double *chi, double *sig_star, double *dpl, double *sbar,
                            cudaStream_t s) {
     const long nc = (long)p.nx * p.ny * p.nz;
-    k_stress_predict<<<nblocks(nc), kThreads, 0, s>>>(p, stz_const(p), v, sig, chi, sig_star, dpl,
-                                                      sbar, nc);
+    k_stress_predict<<<cell_grid(p.nx, p.ny, p.nz), kBlock, 0, s>>>(p, stz_const(p), v, sig, chi,
+                                                                    sig_star, dpl, sbar, nc);
     count_launch();
     return cudaGetLastError();
 }
@@ -254,15 +257,14 @@ cudaError_t stress_predict(const StepParams &p, const double *v, const double *s
 cudaError_t chi_update(const StepParams &p, const double *sig, const double *chi,
                        const double *dpl, const double *sbar, double *chi_new, cudaStream_t s) {
     const long nc = (long)p.nx * p.ny * p.nz;
-    k_chi_update<<<nblocks(nc), kThreads, 0, s>>>(p, stz_const(p), sig, chi, dpl, sbar, chi_new,
-                                                  nc);
+    k_chi_update<<<cell_grid(p.nx, p.ny, p.nz), kBlock, 0, s>>>(p, stz_const(p), sig, chi, dpl,
+                                                                sbar, chi_new, nc);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t div_rhs(const StepParams &p, const double *sig_star, double *b, cudaStream_t s) {
     const long pl = (long)p.nx * p.ny;
-    const long tot = pl * (p.nz - 1);
     const double scale = p.h * p.h / (p.mu * p.dt) * (0.25 / p.h);
     cudaError_t e;
     const long cs = (long)(p.nz + 1) * pl;
@@ -272,7 +274,7 @@ cudaError_t div_rhs(const StepParams &p, const double *sig_star, double *b, cuda
         e = cudaMemsetAsync(b + a * cs + (long)p.nz * pl, 0, pl * sizeof(double), s);
         if (e != cudaSuccess) return e;
     }
-    k_div_rhs<<<nblocks(tot), kThreads, 0, s>>>(p, sig_star, b, tot, scale);
+    k_div_rhs<<<cell_grid(p.nx, p.ny, p.nz - 1), kBlock, 0, s>>>(p, sig_star, b, scale);
     count_launch();
     return cudaGetLastError();
 }
@@ -280,14 +282,14 @@ cudaError_t div_rhs(const StepParams &p, const double *sig_star, double *b, cuda
 cudaError_t stress_correct(const StepParams &p, const double *v, const double *sig_star,
                            double *sig, const double *chi_src, double *chi_dst, cudaStream_t s) {
     const long nc = (long)p.nx * p.ny * p.nz;
-    k_stress_correct<<<nblocks(nc), kThreads, 0, s>>>(p, v, sig_star, sig, chi_src, chi_dst, nc);
+    k_stress_correct<<<cell_grid(p.nx, p.ny, p.nz), kBlock, 0, s>>>(p, v, sig_star, sig, chi_src,
+                                                                    chi_dst, nc);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t wall_fill(const WallParams &w, double *v, cudaStream_t s) {
-    const long pl = (long)w.nx * w.ny;
-    k_wall_fill<<<nblocks(pl), kThreads, 0, s>>>(w, v);
+    k_wall_fill<<<cell_grid(w.nx, w.ny, 1), kBlock, 0, s>>>(w, v);
     count_launch();
     return cudaGetLastError();
 }
