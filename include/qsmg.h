@@ -54,7 +54,10 @@ typedef enum {
 
 enum { MG_FP64 = 0, MG_MIXED = 1 };
 /* mg_opts.flags */
-enum { MG_FLAG_COLOUR_PASSES = 1 /* FP32 finest level: one launch per colour */ };
+enum {
+    MG_FLAG_COLOUR_PASSES = 1, /* FP32 sweeps: one launch per colour */
+    MG_FLAG_NO_GRAPH = 2       /* FP32 inner cycles: plain launches, no CUDA graph */
+};
 enum { MG_HIST = 128 };
 
 /* Grid: nx, ny even and >= 4, nz even and >= 2 (cells); h spacing (m). */
@@ -93,12 +96,14 @@ typedef struct {
  *                 coarsest solve).
  *   nu1, nu2      pre/post Gauss-Seidel sweeps (section 3.6 uses 2 and 2).
  *   max_cycles    cap on V-cycles per solve (<= MG_HIST - 1).
- *   inner_cycles  MG_MIXED: FP32 V-cycles per outer refinement step; 0 picks
- *                 the count per step from the FP64 residual and the observed
- *                 V-cycle contraction (at most 10).
- *   flags         0, or MG_FLAG_COLOUR_PASSES to run the FP32 finest-level
- *                 sweeps as eight colour launches instead of the tiled
- *                 two-phase kernel (same arithmetic; kept for comparison).
+ *   inner_cycles  MG_MIXED: FP32 V-cycles per outer refinement step (<= 10);
+ *                 0 picks the count per step from the FP64 residual and the
+ *                 observed V-cycle contraction.
+ *   flags         0 or an OR of: MG_FLAG_COLOUR_PASSES runs FP32 sweeps as
+ *                 eight colour launches instead of the tiled two-phase
+ *                 kernels; MG_FLAG_NO_GRAPH issues the FP32 inner cycles as
+ *                 plain launches instead of replaying a CUDA graph captured
+ *                 at their first use (same arithmetic; kept for comparison).
  */
 typedef struct {
     int precision;

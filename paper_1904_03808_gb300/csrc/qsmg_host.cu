@@ -29,6 +29,17 @@ void set_err(const char *fmt, ...) {
 constexpr int kMaxLev = 16;
 constexpr int kMaxCoarse = 3072;
 constexpr int kProfSlots = 64;
+constexpr int kMaxInner = 10;  // cap on FP32 V-cycles per refinement step
+
+// n FP32 V-cycles (from e = 0) captured once and replayed; the event pairs
+// around its finest-level smoothing calls are recorded by every replay
+struct InnerGraph {
+    cudaGraphExec_t exec = nullptr;
+    long kernels = 0;
+    int nev = 0;
+    cudaEvent_t ev[2 * kMaxInner][2];
+    long sweeps[2 * kMaxInner], launches[2 * kMaxInner];
+};
 
 }  // namespace
 
@@ -67,8 +78,13 @@ struct mg_ctx {
     // finest-level smoothing timers (event pairs recorded on st)
     bool prof_on, prof_events;
     cudaEvent_t ev[kProfSlots][2];
+    cudaEvent_t pend_ev[kProfSlots][2];
     long pend_sweeps[kProfSlots], pend_launches[kProfSlots];
     int npend;
+    // FP32 inner V-cycles as CUDA graphs, one per cycle count
+    InnerGraph *graphs[kMaxInner + 1];
+    cudaStream_t cap;  // private stream used only to capture them
+    InnerGraph *capturing;
     double prof_ms;
     long prof_sweeps, prof_launches;
     std::vector<void *> allocs;
@@ -263,7 +279,7 @@ size_t corner_count(const Dims &d) { return 3 * (size_t)d.cs; }
 mg_status prof_drain(mg_ctx *ctx) {
     for (int i = 0; i < ctx->npend; i++) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]));
+        CK(cudaEventElapsedTime(&ms, ctx->pend_ev[i][0], ctx->pend_ev[i][1]));
         ctx->prof_ms += ms;
         ctx->prof_sweeps += ctx->pend_sweeps[i];
         ctx->prof_launches += ctx->pend_launches[i];
@@ -382,21 +398,53 @@ mg_status sweeps<float>(mg_ctx *ctx, int l, const float *b, float *x, int n, boo
     return sweeps_colour<float>(ctx, l, b, x, n, descending);
 }
 
-template <typename T>
-mg_status smooth(mg_ctx *ctx, int l, const T *b, T *x, int sweeps_n, bool descending) {
-    const bool timed = ctx->prof_on && l == 0 && sweeps_n > 0;
-    if (timed && ctx->npend == kProfSlots) {
+// queue one timed event pair for the next drain
+mg_status prof_push(mg_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1, long sweeps, long launches) {
+    if (ctx->npend == kProfSlots) {
         CK(cudaStreamSynchronize(ctx->st));
         CKS(prof_drain(ctx));
     }
+    ctx->pend_ev[ctx->npend][0] = e0;
+    ctx->pend_ev[ctx->npend][1] = e1;
+    ctx->pend_sweeps[ctx->npend] = sweeps;
+    ctx->pend_launches[ctx->npend] = launches;
+    ctx->npend++;
+    return MG_OK;
+}
+
+template <typename T>
+mg_status smooth(mg_ctx *ctx, int l, const T *b, T *x, int sweeps_n, bool descending) {
+    InnerGraph *G = ctx->capturing;
+    const bool timed = l == 0 && sweeps_n > 0 &&
+                       (G ? G->nev < 2 * kMaxInner : ctx->prof_on);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed && !G) {
+        if (ctx->npend == kProfSlots) {
+            CK(cudaStreamSynchronize(ctx->st));
+            CKS(prof_drain(ctx));
+        }
+        e0 = ctx->ev[ctx->npend][0];
+        e1 = ctx->ev[ctx->npend][1];
+    } else if (timed) {
+        e0 = G->ev[G->nev][0];
+        e1 = G->ev[G->nev][1];
+    }
+    // inside a capture an external record node is needed for the replay to
+    // take a timestamp (a plain record only marks a capture position)
+    const unsigned rec = G ? cudaEventRecordExternal : cudaEventRecordDefault;
     const long launches0 = g_launches.load();
-    if (timed) CK(cudaEventRecord(ctx->ev[ctx->npend][0], ctx->st));
+    if (timed) CK(cudaEventRecordWithFlags(e0, ctx->st, rec));
     CKS(sweeps<T>(ctx, l, b, x, sweeps_n, descending));
     if (timed) {
-        CK(cudaEventRecord(ctx->ev[ctx->npend][1], ctx->st));
-        ctx->pend_sweeps[ctx->npend] = sweeps_n;
-        ctx->pend_launches[ctx->npend] = g_launches.load() - launches0;
-        ctx->npend++;
+        CK(cudaEventRecordWithFlags(e1, ctx->st, rec));
+        const long nl = g_launches.load() - launches0;
+        if (G) {
+            G->sweeps[G->nev] = sweeps_n;
+            G->launches[G->nev] = nl;
+            G->nev++;
+        } else {
+            CKS(prof_push(ctx, e0, e1, sweeps_n, nl));
+        }
     }
     return MG_OK;
 }
@@ -486,7 +534,6 @@ mg_status solve_fp64(mg_ctx *ctx, const double *b, double *v, double tol, mg_sta
 // With 0 the count is chosen per step: enough cycles to bring the FP64
 // residual to tol at the contraction factor observed so far (initially 0.4),
 // at least 1 and at most kMaxInner, so that few FP64 residuals are needed.
-constexpr int kMaxInner = 10;
 
 int inner_count(const mg_ctx *ctx, double rel, double tol, double kappa) {
     if (ctx->opts.inner_cycles > 0) return ctx->opts.inner_cycles;
@@ -494,6 +541,54 @@ int inner_count(const mg_ctx *ctx, double rel, double tol, double kappa) {
     const double need = log(0.7 * tol / rel) / log(kappa);
     int n = (int)ceil(need);
     return n < 1 ? 1 : (n > kMaxInner ? kMaxInner : n);
+}
+
+// n FP32 V-cycles on the finest correction equation from e = 0
+mg_status inner_cycles_direct(mg_ctx *ctx, int n) {
+    CK(cudaMemsetAsync(ctx->x32[0], 0, corner_count(ctx->L[0]) * sizeof(float), ctx->st));
+    for (int c = 0; c < n; c++) CKS(vcycle<float>(ctx, 0, ctx->b32[0], ctx->x32[0]));
+    return MG_OK;
+}
+
+// the same as one CUDA graph: captured on the private stream at first use,
+// replayed on the context's stream
+mg_status inner_cycles(mg_ctx *ctx, int n) {
+    if (ctx->opts.flags & MG_FLAG_NO_GRAPH) return inner_cycles_direct(ctx, n);
+    InnerGraph *G = ctx->graphs[n];
+    if (!G) {
+        G = new InnerGraph();
+        ctx->graphs[n] = G;
+        for (int i = 0; i < 2 * kMaxInner; i++) {
+            CK(cudaEventCreate(&G->ev[i][0]));
+            CK(cudaEventCreate(&G->ev[i][1]));
+        }
+        cudaStream_t user = ctx->st;
+        const long k0 = g_launches.load();
+        CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+        ctx->st = ctx->cap;
+        ctx->capturing = G;
+        const mg_status body = inner_cycles_direct(ctx, n);
+        ctx->capturing = nullptr;
+        ctx->st = user;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(ctx->cap, &graph);
+        G->kernels = g_launches.load() - k0;
+        g_launches.fetch_sub(G->kernels);  // counted when replayed, not when captured
+        if (body != MG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return body;
+        }
+        CK(ee);
+        const cudaError_t ei = cudaGraphInstantiate(&G->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei);
+    }
+    CK(cudaGraphLaunch(G->exec, ctx->st));
+    count_launch(G->kernels);
+    if (ctx->prof_on)
+        for (int i = 0; i < G->nev; i++)
+            CKS(prof_push(ctx, G->ev[i][0], G->ev[i][1], G->sweeps[i], G->launches[i]));
+    return MG_OK;
 }
 
 mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_stats *st) {
@@ -512,7 +607,6 @@ mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_st
     st->resid_hist[0] = rel;
     int outer = 0, cycles = 0;
     double kappa = 0.4;  // V-cycle contraction estimate, refined from the history
-    const size_t n0 = corner_count(ctx->L[0]);
     for (;;) {
         st->rel_resid = rel;
         st->cycles = cycles;
@@ -531,8 +625,7 @@ mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_st
             return MG_OK;
         }
         const int n = inner_count(ctx, rel, tol, kappa);
-        CK(cudaMemsetAsync(ctx->x32[0], 0, n0 * sizeof(float), ctx->st));
-        for (int c = 0; c < n; c++) CKS(vcycle<float>(ctx, 0, ctx->b32[0], ctx->x32[0]));
+        CKS(inner_cycles(ctx, n));
         CK(axpy_f32(ctx->L[0], scale, ctx->x32[0], v, ctx->st));
         outer++;
         cycles += n;
@@ -621,6 +714,17 @@ void mg_free(mg_ctx *ctx) {
             cudaEventDestroy(ctx->ev[i][0]);
             cudaEventDestroy(ctx->ev[i][1]);
         }
+    for (int n = 0; n <= kMaxInner; n++) {
+        InnerGraph *G = ctx->graphs[n];
+        if (!G) continue;
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        for (int i = 0; i < 2 * kMaxInner; i++) {
+            if (G->ev[i][0]) cudaEventDestroy(G->ev[i][0]);
+            if (G->ev[i][1]) cudaEventDestroy(G->ev[i][1]);
+        }
+        delete G;
+    }
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
 }
 
@@ -646,7 +750,7 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         return MG_ERR_ARG;
     }
     if (opts->nu1 < 0 || opts->nu2 < 0 || opts->max_cycles < 0 || opts->max_cycles >= MG_HIST ||
-        opts->inner_cycles < 0) {
+        opts->inner_cycles < 0 || opts->inner_cycles > kMaxInner) {
         set_err("mg_setup: bad nu1/nu2/max_cycles/inner_cycles");
         return MG_ERR_ARG;
     }
@@ -745,6 +849,11 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         ALLOC(ctx->rhs, corner_count(ctx->L[0]));
     }
 #undef ALLOC
+    if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        set_err("cudaStreamCreateWithFlags failed");
+        s = MG_ERR_CUDA;
+        goto fail;
+    }
     if (cudaMallocHost((void **)&ctx->hsum, sizeof(double)) != cudaSuccess) {
         set_err("cudaMallocHost failed");
         s = MG_ERR_OOM;

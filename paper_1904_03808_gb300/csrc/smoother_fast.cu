@@ -151,7 +151,7 @@ struct CoarseOp {
 // the 19-point one needs about 40
 template <class Op>
 struct MinBlocks {
-    static constexpr int value = 4;
+    static constexpr int value = 6;
 };
 template <>
 struct MinBlocks<CoarseOp<float>> {

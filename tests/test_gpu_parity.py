@@ -241,6 +241,26 @@ def test_mixed_solve_reaches_tolerance(shape, inner):
     assert err <= 1e-6, err
 
 
+@pytest.mark.parametrize("inner", [0, 4])
+def test_mixed_graph_replay_equals_direct_launches(inner):
+    """The FP32 inner cycles replayed from CUDA graphs give bitwise the same
+    iterate as the same kernels launched one by one."""
+    shape = (32, 32, 32)
+    b = I.rhs_field(4, *shape)
+    v = np.zeros_like(b)
+    v[0, 0], v[0, 32] = -1.0, 1.0
+    outs = []
+    for flags in (0, 2):
+        ctx = ctx_for(shape, precision=MG_MIXED, max_cycles=30, inner_cycles=inner, flags=flags)
+        for _ in range(2):  # the second solve replays the captured graphs
+            vg = g(v)
+            st, s = ctx.solve(g(b), vg, tol=1e-10)
+        outs.append((c(vg), s.cycles, s.outer_iters, s.rel_resid))
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1:] == outs[1][1:]
+
+
 def test_zero_rhs_gives_zero_and_status_codes():
     shape = (16, 16, 16)
     ctx = ctx_for(shape, max_cycles=3)
