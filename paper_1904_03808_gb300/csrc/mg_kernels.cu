@@ -19,6 +19,12 @@ inline unsigned nblocks(long n, int t = kThreads) { return (unsigned)((n + t - 1
 // finest-level operator (structured 19-point stencil)
 // ---------------------------------------------------------------------------
 
+// column position of x index i in a row: natural, or parity-split (the even
+// nodes of the row first, then the odd ones; used for the finest FP32 arrays)
+__device__ __forceinline__ int colmap(int i, int nx, int split) {
+    return split ? ((i & 1) * (nx >> 1) + (i >> 1)) : i;
+}
+
 // value of x at plane kk; with WO ("walls only") interior planes read as zero
 template <typename T, bool WO>
 __device__ __forceinline__ T ldx(const T *x, long idx, int kk, int nz) {
@@ -30,11 +36,13 @@ __device__ __forceinline__ T ldx(const T *x, long idx, int kk, int nz) {
 //   = -( lp x_a(+-e_a) + x_a(+-e_b, b != a) + kq sum_{b!=a} M_ab[x_b] ),
 // M_ab[g] = g(+a,+b) - g(+a,-b) - g(-a,+b) + g(-a,-b)  (4-point mixed difference)
 template <typename T, bool WO>
-__device__ __forceinline__ void fine_off(const T *x, const Dims &d, int i, int j, int k, T lp, T kq,
-                                         T o[3]) {
+__device__ __forceinline__ void fine_off(const T *x, const Dims &d, int i0, int j, int k, T lp,
+                                         T kq, T o[3], int split = 0) {
     const int nx = d.nx, ny = d.ny, nz = d.nz;
     const long ps = (long)nx * ny;
-    const int im = i ? i - 1 : nx - 1, ip = (i + 1 < nx) ? i + 1 : 0;
+    const int im = colmap(i0 ? i0 - 1 : nx - 1, nx, split),
+              ip = colmap((i0 + 1 < nx) ? i0 + 1 : 0, nx, split);
+    const int i = colmap(i0, nx, split);
     const int jm = j ? j - 1 : ny - 1, jp = (j + 1 < ny) ? j + 1 : 0;
     const long pc = (long)k * ps, pm = pc - ps, pp = pc + ps;
     const long r0 = (long)j * nx, rm = (long)jm * nx, rp = (long)jp * nx;
@@ -153,12 +161,12 @@ __global__ void k_gs_coarse(Dims d, Coarse<T> c, const T *__restrict__ b, T *x, 
 
 template <typename T>
 __global__ void k_res_fine(Dims d, Fine<T> f, const T *__restrict__ b, const T *__restrict__ x,
-                           T *__restrict__ r) {
+                           T *__restrict__ r, int split) {
     int i, j, k;
     if (!node_ijk(d, i, j, k)) return;
     T o[3];
-    fine_off<T, false>(x, d, i, j, k, f.lp, f.kq, o);
-    const long p = ((long)k * d.ny + j) * d.nx + i;
+    fine_off<T, false>(x, d, i, j, k, f.lp, f.kq, o, split);
+    const long p = ((long)k * d.ny + j) * d.nx + colmap(i, d.nx, split);
 #pragma unroll
     for (int a = 0; a < 3; a++) r[p + a * d.cs] = b[p + a * d.cs] - (f.d0 * x[p + a * d.cs] + o[a]);
 }
@@ -202,7 +210,7 @@ template <bool WO>
 __global__ void __launch_bounds__(kRedThreads)
     k_res_norm_fine64(Dims d, Fine<double> f, const double *__restrict__ b,
                       const double *__restrict__ x, float *__restrict__ r32, double out_scale,
-                      double *__restrict__ partials) {
+                      double *__restrict__ partials, int split32) {
     // rows (j, k) are dealt to blocks in a fixed order, columns to threads,
     // so the partial sums do not depend on timing
     double acc = 0.0;
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(kRedThreads)
                 const double xc = WO ? 0.0 : x[p + a * d.cs];
                 const double r = b[p + a * d.cs] - (f.d0 * xc + o[a]);
                 acc += r * r;
-                if (r32) r32[p + a * d.cs] = (float)(r * out_scale);
+                if (r32) r32[p - i + colmap(i, d.nx, split32) + a * d.cs] = (float)(r * out_scale);
             }
         }
     }
@@ -265,7 +273,8 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double *__restrict_
 // restriction R = T^T (full weighting, weights 1, 1/2, 1/4, 1/8 by the
 // number of odd offsets), coarse interior nodes
 template <typename T>
-__global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restrict__ bc) {
+__global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restrict__ bc,
+                           int split) {
     int I, J, K;
     if (!node_ijk(c, I, J, K)) return;
     T s0 = 0, s1 = 0, s2 = 0;
@@ -284,7 +293,7 @@ __global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restric
                 const T w = (ex ? T(0.5) : T(1)) * wy * wz;
                 int ii = 2 * I + ex;
                 ii = ii < 0 ? ii + f.nx : (ii >= f.nx ? ii - f.nx : ii);
-                const long q = row + ii;
+                const long q = row + colmap(ii, f.nx, split);
                 s0 += w * r[q];
                 s1 += w * r[q + f.cs];
                 s2 += w * r[q + 2 * f.cs];
@@ -300,7 +309,7 @@ __global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restric
 // prolongation x += T xc: fine node 2I is coarse node I, odd fine nodes take
 // the mean of their two neighbours along each odd axis (coarse walls are 0)
 template <typename T>
-__global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restrict__ x) {
+__global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restrict__ x, int split) {
     int i, j, k;
     if (!node_ijk(f, i, j, k)) return;
     const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
@@ -310,7 +319,7 @@ __global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restric
     const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1), wz = (k & 1) ? T(0.5) : T(1);
     const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
     const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
-    const long p = ((long)k * f.ny + j) * f.nx + i;
+    const long p = ((long)k * f.ny + j) * f.nx + colmap(i, f.nx, split);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         T s = 0;
@@ -355,12 +364,25 @@ __global__ void k_zero_interior(Dims d, double *__restrict__ x) {
 }
 
 __global__ void k_axpy_f32(Dims d, double scale, const float *__restrict__ e,
-                           double *__restrict__ v) {
+                           double *__restrict__ v, int split) {
     int i, j, k;
     if (!node_ijk(d, i, j, k)) return;
-    const long p = ((long)k * d.ny + j) * d.nx + i;
+    const long row = ((long)k * d.ny + j) * d.nx;
+    const long p = row + i, pe = row + colmap(i, d.nx, split);
 #pragma unroll
-    for (int a = 0; a < 3; a++) v[a * d.cs + p] += scale * (double)e[a * d.cs + p];
+    for (int a = 0; a < 3; a++) v[a * d.cs + p] += scale * (double)e[a * d.cs + pe];
+}
+
+// natural <-> parity-split column order of a whole corner array
+template <bool TO_SPLIT>
+__global__ void k_split(Dims d, const float *__restrict__ src, float *__restrict__ dst) {
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int kc = blockIdx.z;  // component * (nz+1) + plane
+    if (i >= d.nx || j >= d.ny) return;
+    const long row = ((long)kc * d.ny + j) * d.nx;
+    const long a = row + i, b = row + colmap(i, d.nx, 1);
+    if (TO_SPLIT) dst[b] = src[a];
+    else dst[a] = src[b];
 }
 
 inline dim3 node_grid(int nx, int ny, int nplanes) {
@@ -409,8 +431,8 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float 
 
 template <typename T>
 static cudaError_t res_fine_t(const Dims &d, const Fine<T> &f, const T *b, const T *x, T *r,
-                              cudaStream_t s) {
-    k_res_fine<T><<<node_grid(d.nx, d.ny, d.nz - 1), kBlock, 0, s>>>(d, f, b, x, r);
+                              cudaStream_t s, int split) {
+    k_res_fine<T><<<node_grid(d.nx, d.ny, d.nz - 1), kBlock, 0, s>>>(d, f, b, x, r, split);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -444,11 +466,11 @@ static cudaError_t res_coarse_t(const Dims &d, const Coarse<T> &c, const T *b, c
 
 cudaError_t residual_fine(const Dims &d, const Fine<double> &f, const double *b, const double *x,
                           double *r, cudaStream_t s) {
-    return res_fine_t(d, f, b, x, r, s);
+    return res_fine_t(d, f, b, x, r, s, 0);
 }
 cudaError_t residual_fine(const Dims &d, const Fine<float> &f, const float *b, const float *x,
-                          float *r, cudaStream_t s) {
-    return res_fine_t(d, f, b, x, r, s);
+                          float *r, cudaStream_t s, int split) {
+    return res_fine_t(d, f, b, x, r, s, split);
 }
 cudaError_t residual_coarse(const Dims &d, const Coarse<double> &c, const double *b,
                             const double *x, double *r, cudaStream_t s) {
@@ -461,13 +483,13 @@ cudaError_t residual_coarse(const Dims &d, const Coarse<float> &c, const float *
 
 cudaError_t residual_norm_fine64(const Dims &d, const Fine<double> &f, const double *b,
                                  const double *x, bool wall_only, float *r32, double out_scale,
-                                 double *partials, cudaStream_t s) {
+                                 double *partials, cudaStream_t s, int split32) {
     if (wall_only)
         k_res_norm_fine64<true><<<kRedBlocks, kRedThreads, 0, s>>>(d, f, b, x, r32, out_scale,
-                                                                   partials);
+                                                                   partials, split32);
     else
         k_res_norm_fine64<false><<<kRedBlocks, kRedThreads, 0, s>>>(d, f, b, x, r32, out_scale,
-                                                                    partials);
+                                                                    partials, split32);
     count_launch();
     return cudaGetLastError();
 }
@@ -485,32 +507,32 @@ cudaError_t sum_partials(const double *partials, double *out, cudaStream_t s) {
 }
 
 template <typename T>
-static cudaError_t restrict_t(const Dims &f, const T *r, T *bc, cudaStream_t s) {
+static cudaError_t restrict_t(const Dims &f, const T *r, T *bc, cudaStream_t s, int split) {
     const Dims c = make_dims(f.nx / 2, f.ny / 2, f.nz / 2);
     if (c.nz < 2) return cudaSuccess;
-    k_restrict<T><<<node_grid(c.nx, c.ny, c.nz - 1), kBlock, 0, s>>>(f, c, r, bc);
+    k_restrict<T><<<node_grid(c.nx, c.ny, c.nz - 1), kBlock, 0, s>>>(f, c, r, bc, split);
     count_launch();
     return cudaGetLastError();
 }
 cudaError_t restrict_fw(const Dims &fine, const double *r, double *bc, cudaStream_t s) {
-    return restrict_t(fine, r, bc, s);
+    return restrict_t(fine, r, bc, s, 0);
 }
-cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_t s) {
-    return restrict_t(fine, r, bc, s);
+cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_t s, int split) {
+    return restrict_t(fine, r, bc, s, split);
 }
 
 template <typename T>
-static cudaError_t prolong_t(const Dims &f, const T *xc, T *x, cudaStream_t s) {
+static cudaError_t prolong_t(const Dims &f, const T *xc, T *x, cudaStream_t s, int split) {
     const Dims c = make_dims(f.nx / 2, f.ny / 2, f.nz / 2);
-    k_prolong<T><<<node_grid(f.nx, f.ny, f.nz - 1), kBlock, 0, s>>>(f, c, xc, x);
+    k_prolong<T><<<node_grid(f.nx, f.ny, f.nz - 1), kBlock, 0, s>>>(f, c, xc, x, split);
     count_launch();
     return cudaGetLastError();
 }
 cudaError_t prolong_add(const Dims &fine, const double *xc, double *x, cudaStream_t s) {
-    return prolong_t(fine, xc, x, s);
+    return prolong_t(fine, xc, x, s, 0);
 }
-cudaError_t prolong_add(const Dims &fine, const float *xc, float *x, cudaStream_t s) {
-    return prolong_t(fine, xc, x, s);
+cudaError_t prolong_add(const Dims &fine, const float *xc, float *x, cudaStream_t s, int split) {
+    return prolong_t(fine, xc, x, s, split);
 }
 
 template <typename T>
@@ -536,8 +558,20 @@ cudaError_t zero_interior(const Dims &d, double *x, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t axpy_f32(const Dims &d, double scale, const float *e, double *v, cudaStream_t s) {
-    k_axpy_f32<<<node_grid(d.nx, d.ny, d.nz - 1), kBlock, 0, s>>>(d, scale, e, v);
+cudaError_t axpy_f32(const Dims &d, double scale, const float *e, double *v, cudaStream_t s,
+                     int split) {
+    k_axpy_f32<<<node_grid(d.nx, d.ny, d.nz - 1), kBlock, 0, s>>>(d, scale, e, v, split);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t split_columns(const Dims &d, const float *src, float *dst, bool to_split,
+                          cudaStream_t s) {
+    const dim3 grid = node_grid(d.nx, d.ny, 3 * (d.nz + 1));
+    if (to_split)
+        k_split<true><<<grid, kBlock, 0, s>>>(d, src, dst);
+    else
+        k_split<false><<<grid, kBlock, 0, s>>>(d, src, dst);
     count_launch();
     return cudaGetLastError();
 }

@@ -71,6 +71,7 @@ struct mg_ctx {
     double *x64[kMaxLev], *b64[kMaxLev], *r64[kMaxLev];
     float *x32[kMaxLev], *b32[kMaxLev], *r32[kMaxLev];
     float *xs32[kMaxLev];  // ping-pong partners of the tiled FP32 sweeps
+    int split0;            // finest FP32 arrays in parity-split column order
     double *Ainv;
     int ncoarse;
     double *partials, *dsum, *hsum;
@@ -302,9 +303,9 @@ mg_status read_sum(mg_ctx *ctx, double *out) {
 // ||b - A v||_2 on the finest level (FP64), optionally writing
 // float(r * out_scale) into r32; wall_only gives ||b_lifted||_2
 mg_status fine_resnorm(mg_ctx *ctx, const double *b, const double *v, bool wall_only, float *r32,
-                       double out_scale, double *norm) {
+                       double out_scale, double *norm, int split32 = 0) {
     CK(residual_norm_fine64(ctx->L[0], ctx->f64, b, v, wall_only, r32, out_scale, ctx->partials,
-                            ctx->st));
+                            ctx->st, split32));
     double s2;
     CKS(read_sum(ctx, &s2));
     *norm = sqrt(s2);
@@ -358,7 +359,7 @@ mg_status sweeps_tiled(mg_ctx *ctx, int l, const float *b, float *x, int sweeps,
     }
     for (int s = 0; s < sweeps; s++) {
         if (l == 0)
-            CK(gs_sweep_fine_tiled(d, ctx->f32, b, a, o, descending, ctx->st));
+            CK(gs_sweep_fine_tiled(d, ctx->f32, b, a, o, descending, ctx->st, ctx->split0));
         else
             CK(gs_sweep_coarse_tiled(d, ctx->c32[l], b, a, o, descending, ctx->st));
         float *t = a;
@@ -392,9 +393,16 @@ mg_status sweeps(mg_ctx *ctx, int l, const T *b, T *x, int n, bool descending) {
     return sweeps_colour<T>(ctx, l, b, x, n, descending);
 }
 
+// FP32: the tiled two-phase kernels, except on large coarse levels where the
+// 27-point tiled kernel (128 registers, 2 CTAs per SM) loses to colour
+// launches (measured on GB300 at 128^2 planes: 71 us per phase launch against
+// 4 x 13 us)
 template <>
 mg_status sweeps<float>(mg_ctx *ctx, int l, const float *b, float *x, int n, bool descending) {
-    if (!(ctx->opts.flags & MG_FLAG_COLOUR_PASSES)) return sweeps_tiled(ctx, l, b, x, n, descending);
+    const Dims &d = ctx->L[l];
+    const bool colour = (ctx->opts.flags & MG_FLAG_COLOUR_PASSES) ||
+                        (l > 0 && (long)d.nx * d.ny >= 128L * 128L);
+    if (!colour) return sweeps_tiled(ctx, l, b, x, n, descending);
     return sweeps_colour<float>(ctx, l, b, x, n, descending);
 }
 
@@ -449,6 +457,16 @@ mg_status smooth(mg_ctx *ctx, int l, const T *b, T *x, int sweeps_n, bool descen
     return MG_OK;
 }
 
+// the solver's FP32 finest-level arrays may be in parity-split column order
+template <typename T>
+int split_of(const mg_ctx *ctx, int l) {
+    return 0;
+}
+template <>
+int split_of<float>(const mg_ctx *ctx, int l) {
+    return l == 0 ? ctx->split0 : 0;
+}
+
 template <typename T>
 mg_status residual_level(mg_ctx *ctx, int l, const T *b, const T *x, T *r) {
     if (l == 0)
@@ -456,6 +474,32 @@ mg_status residual_level(mg_ctx *ctx, int l, const T *b, const T *x, T *r) {
     else
         CK(residual_coarse(ctx->L[l], Bufs<T>::coarse(ctx, l), b, x, r, ctx->st));
     return MG_OK;
+}
+
+template <>
+mg_status residual_level<float>(mg_ctx *ctx, int l, const float *b, const float *x, float *r) {
+    if (l == 0)
+        CK(residual_fine(ctx->L[0], ctx->f32, b, x, r, ctx->st, ctx->split0));
+    else
+        CK(residual_coarse(ctx->L[l], ctx->c32[l], b, x, r, ctx->st));
+    return MG_OK;
+}
+
+inline cudaError_t restrict_fw_any(const Dims &d, const double *r, double *bc, cudaStream_t s,
+                                   int) {
+    return restrict_fw(d, r, bc, s);
+}
+inline cudaError_t restrict_fw_any(const Dims &d, const float *r, float *bc, cudaStream_t s,
+                                   int split) {
+    return restrict_fw(d, r, bc, s, split);
+}
+inline cudaError_t prolong_add_any(const Dims &d, const double *xc, double *x, cudaStream_t s,
+                                   int) {
+    return prolong_add(d, xc, x, s);
+}
+inline cudaError_t prolong_add_any(const Dims &d, const float *xc, float *x, cudaStream_t s,
+                                   int split) {
+    return prolong_add(d, xc, x, s, split);
 }
 
 // one V-cycle for A_l x = b on level l (section 3.6)
@@ -470,10 +514,10 @@ mg_status vcycle(mg_ctx *ctx, int l, const T *b, T *x) {
     CKS(smooth<T>(ctx, l, b, x, ctx->opts.nu1, false));
     CKS(residual_level<T>(ctx, l, b, x, r));
     T *bc = Bufs<T>::b(ctx, l + 1), *xc = Bufs<T>::x(ctx, l + 1);
-    CK(restrict_fw(ctx->L[l], r, bc, ctx->st));
+    CK(restrict_fw_any(ctx->L[l], r, bc, ctx->st, split_of<T>(ctx, l)));
     CK(cudaMemsetAsync(xc, 0, corner_count(ctx->L[l + 1]) * sizeof(T), ctx->st));
     CKS(vcycle<T>(ctx, l + 1, bc, xc));
-    CK(prolong_add(ctx->L[l], xc, x, ctx->st));
+    CK(prolong_add_any(ctx->L[l], xc, x, ctx->st, split_of<T>(ctx, l)));
     CKS(smooth<T>(ctx, l, b, x, ctx->opts.nu2, true));
     return MG_OK;
 }
@@ -602,7 +646,7 @@ mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_st
         return MG_OK;
     }
     double scale = bn;
-    CKS(fine_resnorm(ctx, b, v, false, ctx->b32[0], 1.0 / scale, &rn));
+    CKS(fine_resnorm(ctx, b, v, false, ctx->b32[0], 1.0 / scale, &rn, ctx->split0));
     double rel = rn / bn;
     st->resid_hist[0] = rel;
     int outer = 0, cycles = 0;
@@ -626,11 +670,11 @@ mg_status solve_mixed(mg_ctx *ctx, const double *b, double *v, double tol, mg_st
         }
         const int n = inner_count(ctx, rel, tol, kappa);
         CKS(inner_cycles(ctx, n));
-        CK(axpy_f32(ctx->L[0], scale, ctx->x32[0], v, ctx->st));
+        CK(axpy_f32(ctx->L[0], scale, ctx->x32[0], v, ctx->st, ctx->split0));
         outer++;
         cycles += n;
         scale = rn;
-        CKS(fine_resnorm(ctx, b, v, false, ctx->b32[0], 1.0 / scale, &rn));
+        CKS(fine_resnorm(ctx, b, v, false, ctx->b32[0], 1.0 / scale, &rn, ctx->split0));
         const double rel_new = rn / bn;
         if (rel_new > 0.0 && rel_new < rel) {
             const double k = pow(rel_new / rel, 1.0 / n);
@@ -785,6 +829,9 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         return MG_ERR_SHAPE;
     }
     ctx->ncoarse = (int)nco;
+    // finest FP32 arrays in parity-split order when the tiled sweeps run on a
+    // grid with coarser levels (so level 0 is never the directly solved one)
+    ctx->split0 = (ctx->nlev > 1 && !(opts->flags & MG_FLAG_COLOUR_PASSES)) ? 1 : 0;
     fine_table(ctx->lam, ctx->mu, ctx->S[0]);
     for (int l = 1; l < ctx->nlev; l++) galerkin_table(ctx->S[l - 1], ctx->S[l]);
     const double lp = (ctx->lam + 2.0 * ctx->mu) / ctx->mu, kq = (ctx->lam + ctx->mu) / (4.0 * ctx->mu);
@@ -962,10 +1009,29 @@ mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps,
         set_err("mg_smooth: bad arguments");
         return MG_ERR_ARG;
     }
-    if (precision == MG_FP64)
+    if (precision == MG_FP64) {
         CKS(smooth<double>(ctx, level, (const double *)b, (double *)x, nsweeps, descending != 0));
-    else
+    } else if (level == 0 && ctx->split0) {
+        // the caller's arrays are in natural order: convert through the
+        // solver's own finest FP32 buffers
+        const Dims &d = ctx->L[0];
+        const size_t plane = (size_t)d.ny * d.nx;
+        CK(split_columns(d, (const float *)x, ctx->x32[0], true, ctx->st));
+        CK(split_columns(d, (const float *)b, ctx->b32[0], true, ctx->st));
+        CK(cudaMemcpyAsync(ctx->xs32[0], ctx->x32[0], 3 * (size_t)d.cs * sizeof(float),
+                           cudaMemcpyDeviceToDevice, ctx->st));  // partner gets the walls
+        CKS(smooth<float>(ctx, 0, ctx->b32[0], ctx->x32[0], nsweeps, descending != 0));
+        CK(split_columns(d, ctx->x32[0], (float *)x, false, ctx->st));
+        // the solver relies on zero walls in x32[0] and its partner
+        for (float *w : {ctx->x32[0], ctx->xs32[0]})
+            for (int c = 0; c < 3; c++) {
+                CK(cudaMemsetAsync(w + c * d.cs, 0, plane * sizeof(float), ctx->st));
+                CK(cudaMemsetAsync(w + c * d.cs + d.nz * plane, 0, plane * sizeof(float),
+                                   ctx->st));
+            }
+    } else {
         CKS(smooth<float>(ctx, level, (const float *)b, (float *)x, nsweeps, descending != 0));
+    }
     CK(cudaStreamSynchronize(ctx->st));
     return MG_OK;
 }

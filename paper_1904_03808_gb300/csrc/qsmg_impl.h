@@ -64,9 +64,11 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<double> &c, const doubl
 cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float *b, float *x,
                              int colour, cudaStream_t s);
 
-// tiled FP32 finest-level sweep vin -> vout (two phase launches)
+// tiled FP32 finest-level sweep vin -> vout (two phase launches); split:
+// the arrays are in parity-split column order
 cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,
-                                const float *vin, float *vout, bool descending, cudaStream_t s);
+                                const float *vin, float *vout, bool descending, cudaStream_t s,
+                                int split = 0);
 
 // tiled FP32 coarse-level sweep vin -> vout (27-point block stencil)
 cudaError_t gs_sweep_coarse_tiled(const Dims &d, const Coarse<float> &c, const float *b,
@@ -76,7 +78,7 @@ cudaError_t gs_sweep_coarse_tiled(const Dims &d, const Coarse<float> &c, const f
 cudaError_t residual_fine(const Dims &d, const Fine<double> &f, const double *b, const double *x,
                           double *r, cudaStream_t s);
 cudaError_t residual_fine(const Dims &d, const Fine<float> &f, const float *b, const float *x,
-                          float *r, cudaStream_t s);
+                          float *r, cudaStream_t s, int split = 0);
 cudaError_t residual_coarse(const Dims &d, const Coarse<double> &c, const double *b,
                             const double *x, double *r, cudaStream_t s);
 cudaError_t residual_coarse(const Dims &d, const Coarse<float> &c, const float *b, const float *x,
@@ -84,19 +86,22 @@ cudaError_t residual_coarse(const Dims &d, const Coarse<float> &c, const float *
 
 // FP64 fine residual with the sum of squares into partials[kRedBlocks];
 // wall_only treats interior x as zero (lifted right-hand side);
-// r32 (optional) receives float(r * out_scale)
+// r32 (optional) receives float(r * out_scale), in parity-split column order
+// if split32
 cudaError_t residual_norm_fine64(const Dims &d, const Fine<double> &f, const double *b,
                                  const double *x, bool wall_only, float *r32, double out_scale,
-                                 double *partials, cudaStream_t s);
+                                 double *partials, cudaStream_t s, int split32 = 0);
 // sum of squares of a level vector's interior into partials
 cudaError_t sumsq(const Dims &d, const double *r, double *partials, cudaStream_t s);
 // out[0] = sum of partials[0..kRedBlocks)
 cudaError_t sum_partials(const double *partials, double *out, cudaStream_t s);
 
 cudaError_t restrict_fw(const Dims &fine, const double *r, double *bc, cudaStream_t s);
-cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_t s);
+cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_t s,
+                        int split = 0);
 cudaError_t prolong_add(const Dims &fine, const double *xc, double *x, cudaStream_t s);
-cudaError_t prolong_add(const Dims &fine, const float *xc, float *x, cudaStream_t s);
+cudaError_t prolong_add(const Dims &fine, const float *xc, float *x, cudaStream_t s,
+                        int split = 0);
 
 // x += Ainv r on the coarsest level (dense FP64 inverse, n unknowns)
 cudaError_t coarse_solve(const Dims &d, const double *Ainv, int n, const double *r, double *x,
@@ -105,8 +110,13 @@ cudaError_t coarse_solve(const Dims &d, const double *Ainv, int n, const float *
                          cudaStream_t s);
 
 cudaError_t zero_interior(const Dims &d, double *x, cudaStream_t s);
-// v += scale * e (interior)
-cudaError_t axpy_f32(const Dims &d, double scale, const float *e, double *v, cudaStream_t s);
+// v += scale * e (interior; e in parity-split column order if split)
+cudaError_t axpy_f32(const Dims &d, double scale, const float *e, double *v, cudaStream_t s,
+                     int split = 0);
+// corner array between natural and parity-split column order (even rows:
+// x = 0, 2, ..., nx-2, then 1, 3, ..., nx-1); nx must be even
+cudaError_t split_columns(const Dims &d, const float *src, float *dst, bool to_split,
+                          cudaStream_t s);
 
 // ---------------------------------------------------------------- step
 struct StepParams {

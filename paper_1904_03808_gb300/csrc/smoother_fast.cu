@@ -13,9 +13,9 @@
 // instead of eight times.
 //
 // Inside one plane a CTA owns a TX x TY tile and stages a window of that plane
-// with a halo of HX columns and HY rows in shared memory (17 KB in FP32, so 8
-// CTAs fit on an SM); the z-neighbour planes and the right-hand side, which
-// the phase only reads, come through the read-only cache.  The same kernel
+// with a halo of HX columns and HY rows in shared memory (17 KB in FP32); the
+// z-neighbour planes and the right-hand side, which the phase only reads,
+// come through the read-only cache.  The same kernel
 // serves the finest level (structured 19-point operator) and the coarse
 // levels (Galerkin 27-point block stencil); both couple a node only to the 8
 // in-plane neighbours and to 9 nodes in each adjacent plane.  The 4 in-plane colours are
@@ -38,9 +38,9 @@ constexpr int WIN1 = WY * WX;          // one component of a window
 constexpr int WIN = 3 * WIN1;          // three components
 constexpr int NT = 256;
 
-template <typename T>
+template <typename T, bool STAGE_Z>
 constexpr size_t smem_bytes() {
-    return WIN * sizeof(T) + (WX + WY) * sizeof(int);
+    return (STAGE_Z ? 3 : 1) * WIN * sizeof(T) + (WX + WY) * sizeof(int);
 }
 
 // window element (component c, row wy, column wx): columns split by parity so
@@ -65,11 +65,16 @@ struct View {
     const T *__restrict__ B;
     long cs;
     const int *rowg, *colg;
+    const T *Ls, *Hs;  // staged z-neighbour windows (operators with kStageZ)
 };
 
-// finest level: the structured 19-point operator (scaled Eq. 30)
+// finest level: the structured 19-point operator (scaled Eq. 30).  Its
+// z-neighbour planes are read through the read-only cache: staging them in
+// shared memory as well was measured slower on GB300 (0.50 against 0.36 ms a
+// sweep at 256^3), the extra staging traffic outweighing the stride-2 reads
 template <typename T>
 struct FineOp {
+    static constexpr bool kStageZ = false;
     Fine<T> f;
     __device__ __forceinline__ void update(const View<T> &v, int wx, int wy) const {
         T *P = v.P;
@@ -109,6 +114,7 @@ struct FineOp {
 // coarse levels: one constant 27-point stencil of 3x3 blocks (Eq. 36)
 template <typename T>
 struct CoarseOp {
+    static constexpr bool kStageZ = false;
     Coarse<T> c;
     __device__ __forceinline__ void update(const View<T> &v, int wx, int wy) const {
         T s0 = 0, s1 = 0, s2 = 0;
@@ -147,7 +153,7 @@ struct CoarseOp {
 };
 
 // resident CTAs per SM the register budget is cut for: the 27-point operator
-// keeps its 243 coefficients in registers (~128 registers a thread in FP32),
+// keeps its 243 coefficients in registers (~128 registers a thread in FP32);
 // the 19-point one needs about 40
 template <class Op>
 struct MinBlocks {
@@ -192,28 +198,66 @@ struct Pair<double> {
 template <typename T, class Op, int F>
 __global__ void __launch_bounds__(NT, MinBlocks<Op>::value)
     k_gs_tiled(Dims d, Op op, const T *__restrict__ b, const T *__restrict__ vin,
-               const T *__restrict__ zsrc, T *__restrict__ vout, int kbase) {
+               const T *__restrict__ zsrc, T *__restrict__ vout, int kbase, int split) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool SZ = Op::kStageZ;
     T *sP = reinterpret_cast<T *>(smem_raw);
-    int *colg = reinterpret_cast<int *>(sP + WIN), *rowg = colg + WX;
+    T *sL = sP + WIN, *sH = sP + 2 * WIN;  // used only when SZ
+    int *colg = reinterpret_cast<int *>(sP + (SZ ? 3 : 1) * WIN), *rowg = colg + WX;
     typedef typename Pair<T>::V V2;
     const int nx = d.nx, ny = d.ny;
     const long ps = (long)nx * ny, cs = d.cs;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int k = 2 * blockIdx.z + kbase;
+    const int hnx = nx >> 1;
     for (int e = threadIdx.x; e < WX + WY; e += NT) {
-        if (e < WX) colg[e] = wrap_mod(x0 - HX + e, nx);
-        else rowg[e - WX] = wrap_mod(y0 - HY + (e - WX), ny) * nx;
+        if (e < WX) {
+            const int gx = wrap_mod(x0 - HX + e, nx);
+            colg[e] = split ? (gx & 1) * hnx + (gx >> 1) : gx;
+        } else {
+            rowg[e - WX] = wrap_mod(y0 - HY + (e - WX), ny) * nx;
+        }
     }
     __syncthreads();
-    // stage the plane's window as (even, odd) column pairs
-    const T *src = vin + (long)k * ps;
-    for (int e = threadIdx.x; e < 3 * WY * WH; e += NT) {
-        const int c = e / (WY * WH), r = e - c * (WY * WH);
-        const int wy = r / WH, h = r - wy * WH;
-        const V2 p2 = __ldg(reinterpret_cast<const V2 *>(src + c * cs + rowg[wy] + colg[2 * h]));
-        sP[widx(c, wy, 2 * h)] = p2.x;
-        sP[widx(c, wy, 2 * h + 1)] = p2.y;
+    // stage the plane's window (and, with SZ, its z-neighbours') as (even,
+    // odd) column pairs: one aligned pair load, two conflict-free stores
+    auto stage = [&](T *dst, const T *src) {
+        if (!split) {
+            for (int e = threadIdx.x; e < 3 * WY * WH; e += NT) {
+                const int c = e / (WY * WH), r = e - c * (WY * WH);
+                const int wy = r / WH, h = r - wy * WH;
+                const V2 p2 =
+                    __ldg(reinterpret_cast<const V2 *>(src + c * cs + rowg[wy] + colg[2 * h]));
+                dst[widx(c, wy, 2 * h)] = p2.x;
+                dst[widx(c, wy, 2 * h + 1)] = p2.y;
+            }
+        } else if ((hnx & 1) == 0) {
+            // parity-split rows, nx a multiple of 4: the window's half-rows
+            // are runs of aligned same-parity pairs (the periodic wrap falls
+            // between pairs)
+            for (int e = threadIdx.x; e < 3 * WY * WH; e += NT) {
+                const int c = e / (WY * WH), r = e - c * (WY * WH);
+                const int wy = r / WH, q = r - wy * WH;
+                const int par = q / (WH / 2), h = 2 * (q - par * (WH / 2)), wx = 2 * h + par;
+                const V2 p2 =
+                    __ldg(reinterpret_cast<const V2 *>(src + c * cs + rowg[wy] + colg[wx]));
+                dst[widx(c, wy, wx)] = p2.x;
+                dst[widx(c, wy, wx + 2)] = p2.y;
+            }
+        } else {
+            // parity-split rows, single values
+            for (int e = threadIdx.x; e < 3 * WY * WX; e += NT) {
+                const int c = e / (WY * WX), r = e - c * (WY * WX);
+                const int wy = r / WX, q = r - wy * WX;
+                const int par = q / WH, h = q - par * WH, wx = 2 * h + par;
+                dst[widx(c, wy, wx)] = __ldg(src + c * cs + rowg[wy] + colg[wx]);
+            }
+        }
+    };
+    stage(sP, vin + (long)k * ps);
+    if (SZ) {
+        stage(sL, zsrc + (long)(k - 1) * ps);
+        stage(sH, zsrc + (long)(k + 1) * ps);
     }
     __syncthreads();
     View<T> v;
@@ -224,6 +268,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<Op>::value)
     v.cs = cs;
     v.rowg = rowg;
     v.colg = colg;
+    v.Ls = sL;
+    v.Hs = sH;
     // the 4 in-plane colours on shrinking regions (window coordinates; the
     // tile is [HX, HX+TX) x [HY, HY+TY))
     colour_pass<T, Op>(v, op, F, F, 1, WX - 1, 1, WY - 1);
@@ -234,62 +280,96 @@ __global__ void __launch_bounds__(NT, MinBlocks<Op>::value)
     __syncthreads();
     colour_pass<T, Op>(v, op, 1 - F, 1 - F, 4, WX - 4, 2, WY - 2);
     __syncthreads();
-    // store the tile (nodes inside the grid only) as pairs
+    // store the tile (nodes inside the grid only)
     T *out = vout + (long)k * ps;
-    for (int e = threadIdx.x; e < 3 * TY * (TX / 2); e += NT) {
-        const int c = e / (TY * (TX / 2)), r = e - c * (TY * (TX / 2));
-        const int ty = r / (TX / 2), h = r - ty * (TX / 2);
-        const int gx = x0 + 2 * h, gy = y0 + ty;
-        if (gx < nx && gy < ny) {
-            V2 p2;
-            p2.x = sP[widx(c, ty + HY, 2 * h + HX)];
-            p2.y = sP[widx(c, ty + HY, 2 * h + HX + 1)];
-            *reinterpret_cast<V2 *>(out + c * cs + (long)gy * nx + gx) = p2;
+    if (!split) {
+        for (int e = threadIdx.x; e < 3 * TY * (TX / 2); e += NT) {
+            const int c = e / (TY * (TX / 2)), r = e - c * (TY * (TX / 2));
+            const int ty = r / (TX / 2), h = r - ty * (TX / 2);
+            const int gx = x0 + 2 * h, gy = y0 + ty;
+            if (gx < nx && gy < ny) {
+                V2 p2;
+                p2.x = sP[widx(c, ty + HY, 2 * h + HX)];
+                p2.y = sP[widx(c, ty + HY, 2 * h + HX + 1)];
+                *reinterpret_cast<V2 *>(out + c * cs + (long)gy * nx + gx) = p2;
+            }
+        }
+    } else if ((hnx & 1) == 0) {
+        // pairs of same-parity nodes (x0/2 is even, so each pair is aligned)
+        for (int e = threadIdx.x; e < 3 * TY * (TX / 2); e += NT) {
+            const int c = e / (TY * (TX / 2)), r = e - c * (TY * (TX / 2));
+            const int ty = r / (TX / 2), q = r - ty * (TX / 2);
+            const int par = q / (TX / 4), h = 2 * (q - par * (TX / 4));
+            const int gx = x0 + 2 * h + par, gy = y0 + ty;
+            if (gx < nx && gy < ny) {
+                V2 p2;
+                p2.x = sP[widx(c, ty + HY, 2 * h + par + HX)];
+                p2.y = sP[widx(c, ty + HY, 2 * h + par + 2 + HX)];
+                *reinterpret_cast<V2 *>(out + c * cs + (long)gy * nx + par * hnx + (gx >> 1)) = p2;
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < 3 * TY * TX; e += NT) {
+            const int c = e / (TY * TX), r = e - c * (TY * TX);
+            const int ty = r / TX, q = r - ty * TX;
+            const int par = q / (TX / 2), h = q - par * (TX / 2);
+            const int gx = x0 + 2 * h + par, gy = y0 + ty;
+            if (gx < nx && gy < ny)
+                out[c * cs + (long)gy * nx + par * hnx + (gx >> 1)] =
+                    sP[widx(c, ty + HY, 2 * h + par + HX)];
         }
     }
 }
 
 template <typename T, class Op, int F>
 cudaError_t launch_phase(const Dims &d, const Op &op, const T *b, const T *vin, const T *zsrc,
-                         T *vout, int par, cudaStream_t s) {
+                         T *vout, int par, cudaStream_t s, int split) {
     // planes of parity par among the interior planes 1..nz-1
     const int kbase = par ? 1 : 2;
     const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
     if (nplanes <= 0) return cudaSuccess;
-    constexpr size_t smem = smem_bytes<T>();
+    constexpr size_t smem = smem_bytes<T, Op::kStageZ>();
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_gs_tiled<T, Op, F>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, nplanes);
-    k_gs_tiled<T, Op, F><<<grid, NT, smem, s>>>(d, op, b, vin, zsrc, vout, kbase);
+    k_gs_tiled<T, Op, F><<<grid, NT, smem, s>>>(d, op, b, vin, zsrc, vout, kbase, split);
     count_launch();
     return cudaGetLastError();
 }
 
 template <typename T, class Op>
 cudaError_t sweep(const Dims &d, const Op &op, const T *b, const T *vin, T *vout,
-                  bool descending, cudaStream_t s) {
+                  bool descending, cudaStream_t s, int split) {
     cudaError_t e;
     if (!descending) {
-        e = launch_phase<T, Op, 0>(d, op, b, vin, vin, vout, 0, s);  // colours 0-3, even planes
+        // colours 0-3 on the even planes, then 4-7 on the odd planes
+        e = launch_phase<T, Op, 0>(d, op, b, vin, vin, vout, 0, s, split);
         if (e != cudaSuccess) return e;
-        return launch_phase<T, Op, 0>(d, op, b, vin, vout, vout, 1, s);  // colours 4-7, odd planes
+        return launch_phase<T, Op, 0>(d, op, b, vin, vout, vout, 1, s, split);
     }
-    e = launch_phase<T, Op, 1>(d, op, b, vin, vin, vout, 1, s);  // colours 7-4, odd planes
+    // colours 7-4 on the odd planes, then 3-0 on the even planes
+    e = launch_phase<T, Op, 1>(d, op, b, vin, vin, vout, 1, s, split);
     if (e != cudaSuccess) return e;
-    return launch_phase<T, Op, 1>(d, op, b, vin, vout, vout, 0, s);  // colours 3-0, even planes
+    return launch_phase<T, Op, 1>(d, op, b, vin, vout, vout, 0, s, split);
 }
 
 }  // namespace
 
 // one 8-colour sweep vin -> vout (vout's wall planes must hold the walls)
 cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,
-                                const float *vin, float *vout, bool descending, cudaStream_t s) {
+                                const float *vin, float *vout, bool descending, cudaStream_t s,
+                                int split) {
     FineOp<float> op{f};
-    return sweep<float>(d, op, b, vin, vout, descending, s);
+    return sweep<float>(d, op, b, vin, vout, descending, s, split);
 }
 
 cudaError_t gs_sweep_coarse_tiled(const Dims &d, const Coarse<float> &c, const float *b,
                                   const float *vin, float *vout, bool descending, cudaStream_t s) {
     CoarseOp<float> op{c};
-    return sweep<float>(d, op, b, vin, vout, descending, s);
+    return sweep<float>(d, op, b, vin, vout, descending, s, 0);
 }
 
 }  // namespace qsmg

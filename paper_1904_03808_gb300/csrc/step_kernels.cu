@@ -24,14 +24,14 @@ __device__ __forceinline__ bool cell_ijk(int nx, int ny, int &i, int &j, int &k)
 }
 
 struct StzConst {
-    double eDT_over_tau0;  // exp(-Delta/(kB T)) / tau0
-    double beta;           // Omega eps0 / (kB T)
+    double half_eDT_over_tau0;  // exp(-Delta/(kB T)) / (2 tau0)
+    double beta;                // Omega eps0 / (kB T)
     double sY, ez_K;
 };
 
 __host__ StzConst stz_const(const StepParams &p) {
     StzConst c;
-    c.eDT_over_tau0 = exp(-p.Delta_K / p.T) / p.tau0;
+    c.half_eDT_over_tau0 = 0.5 * exp(-p.Delta_K / p.T) / p.tau0;
     c.beta = p.Omega * p.eps0 / (p.kB * p.T);
     c.sY = p.sY;
     c.ez_K = p.ez_K;
@@ -39,11 +39,16 @@ __host__ StzConst stz_const(const StepParams &p) {
 }
 
 // athermal STZ rate magnitude, Eqs. (20)-(22):
-// D = exp(-e_z/(kB chi)) exp(-Delta/(kB T)) cosh(Omega eps0 sbar/(kB T)) (1 - s_Y/sbar) / tau0
-// and 0 at or below yield (or for chi <= 0)
-__device__ __forceinline__ double stz_rate(const StzConst &c, double sbar, double chi) {
+//   D = exp(-e_z/(kB chi)) exp(-Delta/(kB T)) cosh(Omega eps0 sbar/(kB T)) (1 - s_Y/sbar) / tau0,
+// 0 at or below yield (or for chi <= 0).  FP64 is slow on this part, so the
+// product exp(-e_z/chi) cosh(beta sbar) is taken as
+// (exp(beta sbar - e_z/chi) + exp(-beta sbar - e_z/chi)) / 2 (two exponentials,
+// no reciprocal) and 1/sbar is computed once by the caller.
+__device__ __forceinline__ double stz_rate(const StzConst &c, double sbar, double inv_sbar,
+                                           double chi) {
     if (!(sbar > c.sY) || !(chi > 0.0)) return 0.0;
-    return exp(-c.ez_K / chi) * c.eDT_over_tau0 * cosh(c.beta * sbar) * (1.0 - c.sY / sbar);
+    const double y = -c.ez_K / chi, x = c.beta * sbar;
+    return (exp(x + y) + exp(y - x)) * c.half_eDT_over_tau0 * (1.0 - c.sY * inv_sbar);
 }
 
 // sbar with sbar^2 = 1/2 sigma0 : sigma0
@@ -91,10 +96,11 @@ __global__ void k_stress_predict(StepParams p, StzConst c, const double *__restr
     // full symmetric matrix
     const double S[3][3] = {{s6[0], s6[5], s6[4]}, {s6[5], s6[1], s6[3]}, {s6[4], s6[3], s6[2]}};
     const double sb = sbar_of(s6);
-    const double D = stz_rate(c, sb, chi[q]);
+    const double inv_sb = sb > 0.0 ? 1.0 / sb : 0.0;
+    const double D = stz_rate(c, sb, inv_sb, chi[q]);
     const double trL = G[0][0] + G[1][1] + G[2][2];
     const double m = (s6[0] + s6[1] + s6[2]) * (1.0 / 3.0);
-    const double pl = (D > 0.0) ? 2.0 * p.mu * D / sb : 0.0;
+    const double pl = (D > 0.0) ? 2.0 * p.mu * D * inv_sb : 0.0;
     // (a, b) pairs of the 6 stored components
     const int ia[6] = {0, 1, 2, 1, 0, 0}, ib[6] = {0, 1, 2, 2, 2, 1};
 #pragma unroll
@@ -147,7 +153,8 @@ __global__ void k_chi_update(StepParams p, StzConst c, const double *__restrict_
 #pragma unroll
             for (int a = 0; a < 6; a++) s6[a] = 2.0 * sig[a * nc + q] - sig[a * nc + q1];
             cn = 2.0 * c0 - chi[q1];
-            Dn = stz_rate(c, sbar_of(s6), cn);
+            const double sbn = sbar_of(s6);
+            Dn = stz_rate(c, sbn, sbn > 0.0 ? 1.0 / sbn : 0.0, cn);
         }
         acc += 0.5 * (D0 + Dn) * (cn - c0);
     }
