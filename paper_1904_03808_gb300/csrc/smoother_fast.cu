@@ -356,6 +356,7 @@ cudaError_t sweep(const Dims &d, const Op &op, const T *b, const T *vin, T *vout
     return launch_phase<T, Op, 1>(d, op, b, vin, vout, vout, 0, s, split);
 }
 
+
 }  // namespace
 
 // one 8-colour sweep vin -> vout (vout's wall planes must hold the walls)

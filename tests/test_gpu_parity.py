@@ -117,7 +117,8 @@ def test_smoother_fp32_fine_level(shape):
     assert rel(c(xg), x32) <= 2e-6
 
 
-@pytest.mark.parametrize("shape", [(72, 40, 16), (16, 8, 12), (8, 4, 2), (136, 72, 32), (64, 32, 32)])
+@pytest.mark.parametrize("shape", [(72, 40, 16), (16, 8, 12), (8, 4, 2), (136, 72, 32), (64, 32, 32),
+                                   (10, 16, 16)])
 @pytest.mark.parametrize("sweeps,descending", [(1, False), (2, False), (1, True), (3, True)])
 def test_tiled_fp32_sweep_equals_colour_passes(shape, sweeps, descending):
     """The tiled two-phase FP32 sweeps reproduce the eight colour launches on
