@@ -56,8 +56,7 @@ enum { MG_FP64 = 0, MG_MIXED = 1 };
 /* mg_opts.flags */
 enum {
     MG_FLAG_COLOUR_PASSES = 1, /* FP32 sweeps: one launch per colour */
-    MG_FLAG_NO_GRAPH = 2,      /* FP32 inner cycles: plain launches, no CUDA graph */
-    MG_FLAG_NO_TAIL = 4        /* FP32 V-cycle: no single-block kernel for the small levels */
+    MG_FLAG_NO_GRAPH = 2       /* FP32 inner cycles: plain launches, no CUDA graph */
 };
 enum { MG_HIST = 128 };
 
@@ -104,9 +103,7 @@ typedef struct {
  *                 eight colour launches instead of the tiled two-phase
  *                 kernels; MG_FLAG_NO_GRAPH issues the FP32 inner cycles as
  *                 plain launches instead of replaying a CUDA graph captured
- *                 at their first use; MG_FLAG_NO_TAIL runs the small coarse
- *                 levels level by level instead of in one thread block
- *                 (same arithmetic; kept for comparison).
+ *                 at their first use (same arithmetic; kept for comparison).
  */
 typedef struct {
     int precision;

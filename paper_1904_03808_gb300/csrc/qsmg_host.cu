@@ -72,8 +72,6 @@ struct mg_ctx {
     float *x32[kMaxLev], *b32[kMaxLev], *r32[kMaxLev];
     float *xs32[kMaxLev];  // ping-pong partners of the tiled FP32 sweeps
     int split0;            // finest FP32 arrays in parity-split column order
-    int tail;              // first level of the single-block FP32 tail (0: none)
-    float *S32[kMaxLev];   // device copies of the coarse stencils (243 + 9 floats)
     double *Ainv;
     int ncoarse;
     double *partials, *dsum, *hsum;
@@ -504,36 +502,9 @@ inline cudaError_t prolong_add_any(const Dims &d, const float *xc, float *x, cud
     return prolong_add(d, xc, x, s, split);
 }
 
-// levels tail..nlev-1 of an FP32 V-cycle in one thread block
-mg_status tail_cycle(mg_ctx *ctx, const float *b, float *x) {
-    int dims[kMaxLev][3];
-    const float *S[kMaxLev];
-    const int nt = ctx->nlev - ctx->tail;
-    for (int i = 0; i < nt; i++) {
-        const Dims &d = ctx->L[ctx->tail + i];
-        dims[i][0] = d.nx;
-        dims[i][1] = d.ny;
-        dims[i][2] = d.nz;
-        S[i] = ctx->S32[ctx->tail + i];
-    }
-    CK(tail_vcycle(dims, nt, S, ctx->Ainv, ctx->ncoarse, ctx->opts.nu1, ctx->opts.nu2, b, x,
-                   ctx->st));
-    return MG_OK;
-}
-
-template <typename T>
-bool use_tail(const mg_ctx *, int) {
-    return false;
-}
-template <>
-bool use_tail<float>(const mg_ctx *ctx, int l) {
-    return ctx->tail > 0 && l == ctx->tail && !(ctx->opts.flags & MG_FLAG_NO_TAIL);
-}
-
 // one V-cycle for A_l x = b on level l (section 3.6)
 template <typename T>
 mg_status vcycle(mg_ctx *ctx, int l, const T *b, T *x) {
-    if (use_tail<T>(ctx, l)) return tail_cycle(ctx, (const float *)b, (float *)x);
     T *r = Bufs<T>::r(ctx, l);
     if (l == ctx->nlev - 1) {
         CKS(residual_level<T>(ctx, l, b, x, r));
@@ -914,7 +885,6 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         ALLOC(ctx->xs32[l], n);
     }
     ALLOC(ctx->Ainv, Ainv.size());
-    for (int l = 1; l < ctx->nlev; l++) ALLOC(ctx->S32[l], (size_t)252);
     ALLOC(ctx->partials, (size_t)kRedBlocks);
     ALLOC(ctx->dsum, (size_t)1);
     {
@@ -926,34 +896,6 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         ALLOC(ctx->rhs, corner_count(ctx->L[0]));
     }
 #undef ALLOC
-    for (int l = 1; l < ctx->nlev; l++) {
-        float t[252];
-        for (int m = 0; m < 243; m++) t[m] = ctx->c32[l].S[m];
-        for (int m = 0; m < 9; m++) t[243 + m] = ctx->c32[l].Dinv[m];
-        if (cudaMemcpyAsync(ctx->S32[l], t, sizeof(t), cudaMemcpyHostToDevice, ctx->st) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(ctx->st) != cudaSuccess) {
-            set_err("mg_setup: stencil upload failed");
-            s = MG_ERR_CUDA;
-            goto fail;
-        }
-    }
-    // single-block tail: the largest coarse level from which every level down
-    // to the coarsest fits in 200 KB of shared memory (at least one smoothed
-    // level above the coarsest, at most six levels)
-    for (int l = 1; l + 1 < ctx->nlev; l++) {
-        if (ctx->nlev - l > 6) continue;
-        int dims[kMaxLev][3];
-        for (int i = l; i < ctx->nlev; i++) {
-            dims[i - l][0] = ctx->L[i].nx;
-            dims[i - l][1] = ctx->L[i].ny;
-            dims[i - l][2] = ctx->L[i].nz;
-        }
-        if (tail_smem_bytes(dims, ctx->nlev - l) <= 200 * 1024) {
-            ctx->tail = l;
-            break;
-        }
-    }
     if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
         set_err("cudaStreamCreateWithFlags failed");
         s = MG_ERR_CUDA;

@@ -118,13 +118,6 @@ cudaError_t axpy_f32(const Dims &d, double scale, const float *e, double *v, cud
 cudaError_t split_columns(const Dims &d, const float *src, float *dst, bool to_split,
                           cudaStream_t s);
 
-// the whole FP32 V-cycle below one level in a single thread block: dims of
-// the tail levels (top first, coarsest last), device stencil copies (243 +
-// 9 floats each), dense coarsest inverse; b, x of the top tail level
-size_t tail_smem_bytes(const int dims[][3], int nlev);
-cudaError_t tail_vcycle(const int dims[][3], int nlev, const float *const *S, const double *Ainv,
-                        int ncoarse, int nu1, int nu2, const float *b, float *x, cudaStream_t s);
-
 // ---------------------------------------------------------------- step
 struct StepParams {
     int nx, ny, nz;

@@ -262,26 +262,6 @@ def test_mixed_graph_replay_equals_direct_launches(inner):
     assert outs[0][1:] == outs[1][1:]
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 64), (48, 32, 16), (128, 128, 64)])
-def test_mixed_tail_block_equals_level_by_level(shape):
-    """The single-block kernel for the small coarse levels gives the same
-    solve as running those levels pass by pass."""
-    nx, ny, nz = shape
-    b = I.rhs_field(6, nx, ny, nz)
-    v = np.zeros_like(b)
-    v[0, 0], v[0, nz] = -1.0, 1.0
-    outs = []
-    for flags in (0, 4):
-        ctx = ctx_for(shape, precision=MG_MIXED, max_cycles=30, inner_cycles=3, flags=flags)
-        vg = g(v)
-        st, s = ctx.solve(g(b), vg, tol=1e-10)
-        assert st == 0 and s.rel_resid <= 1e-10
-        outs.append((c(vg), s.cycles))
-        ctx.close()
-    assert outs[0][1] == outs[1][1]
-    assert rel(outs[0][0], outs[1][0]) <= 1e-9
-
-
 def test_zero_rhs_gives_zero_and_status_codes():
     shape = (16, 16, 16)
     ctx = ctx_for(shape, max_cycles=3)
