@@ -865,6 +865,14 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         delete ctx;
         return MG_ERR_ARG;
     }
+    {
+        const cudaError_t e = smoother_init();
+        if (e != cudaSuccess) {
+            set_err("mg_setup: %s", cudaGetErrorString(e));
+            delete ctx;
+            return MG_ERR_CUDA;
+        }
+    }
     // buffers
     mg_status s = MG_OK;
 #define ALLOC(p, n)                      \

@@ -64,6 +64,8 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<double> &c, const doubl
 cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float *b, float *x,
                              int colour, cudaStream_t s);
 
+// one-time kernel attribute set-up of the sweeps (call before any capture)
+cudaError_t smoother_init();
 // tiled FP32 finest-level sweep vin -> vout (two phase launches); split:
 // the arrays are in parity-split column order
 cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,

@@ -118,12 +118,13 @@ def test_smoother_fp32_fine_level(shape):
 
 
 @pytest.mark.parametrize("shape", [(72, 40, 16), (16, 8, 12), (8, 4, 2), (136, 72, 32), (64, 32, 32),
-                                   (10, 16, 16)])
+                                   (10, 16, 16), (1024, 64, 64)])
 @pytest.mark.parametrize("sweeps,descending", [(1, False), (2, False), (1, True), (3, True)])
 def test_tiled_fp32_sweep_equals_colour_passes(shape, sweeps, descending):
     """The tiled two-phase FP32 sweeps reproduce the eight colour launches on
     every smoothed level (ragged tiles, odd sweep counts, non-zero walls on the
-    finest level, both colour orders)."""
+    finest level, both colour orders); rows of up to 512 nodes take the
+    row-strip kernel on the finest level, wider rows (1024) the tile kernel."""
     rng = np.random.default_rng(7)
     ctxs = [ctx_for(shape, precision=MG_MIXED, flags=f) for f in (0, 1)]
     nlev = ctxs[0].levels
