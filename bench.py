@@ -11,6 +11,10 @@ random right-hand side are timed beside it.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).
+
+        python bench.py --sweep-only [--n N] [--nz NZ] [--steps K]
+times K finest-level FP32 sweeps alone (two per call, random data, one GPU)
+and prints their mean duration; the small case for kernel profiles.
 """
 from __future__ import annotations
 
@@ -46,7 +50,39 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--inner", type=int, default=INNER)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-only", action="store_true")
+    ap.add_argument("--nz", type=int, default=0)
     return ap.parse_args()
+
+
+def run_sweeps(args):
+    """Finest-level FP32 sweeps in isolation: nx = ny = n, nz (default n) cells."""
+    import torch
+
+    from paper_1904_03808_gb300 import MG_MIXED, Context
+    from paper_1904_03808_gb300 import inputs as I
+    n, nz = args.n, args.nz or args.n
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    ctx = Context(n, n, nz, 2.0e-2 / n, I.TABLE1["K"], I.TABLE1["mu"], precision=MG_MIXED,
+                  stream=stream)
+    g = torch.Generator(device=dev).manual_seed(5)
+    x = torch.rand((3, nz + 1, n, n), device=dev, dtype=torch.float32, generator=g) - 0.5
+    b = torch.rand((3, nz + 1, n, n), device=dev, dtype=torch.float32, generator=g) - 0.5
+    for _ in range(max(args.warmup, 3)):
+        ctx.smooth(0, b, x, 2, False)
+    ctx.profile(True)
+    for _ in range(args.steps):
+        ctx.smooth(0, b, x, 2, False)
+    torch.cuda.synchronize()
+    sm_ms, sweeps, launches = ctx.profile_read()
+    ctx.profile(False)
+    ctx.close()
+    t = sm_ms / max(sweeps, 1)
+    nodes = n * n * (nz - 1)
+    return {"mode": "sweep-only", "grid": [n, n, nz], "sweeps": sweeps, "sweep_ms": t,
+            "achieved_gbs": SMOOTH_BYTES * nodes / (t / 1e3) / 1e9,
+            "launches_per_sweep": launches / max(sweeps, 1)}
 
 
 def workload(n):
@@ -389,7 +425,10 @@ def run_reference(args):
 
 def main():
     args = parse()
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.sweep_only:
+        out = run_sweeps(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out))
 

@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqsmg.so")
-SOURCES = ["mg_kernels.cu", "smoother_fast.cu", "step_kernels.cu", "qsmg_host.cu",
-           "static_scratch.cu"]
+SOURCES = ["mg_kernels.cu", "smoother_fast.cu", "smoother_rows.cu", "step_kernels.cu",
+           "qsmg_host.cu", "static_scratch.cu"]
 HEADERS = ["qsmg_impl.h", os.path.join("..", "..", "include", "qsmg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]

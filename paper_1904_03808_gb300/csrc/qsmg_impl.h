@@ -66,6 +66,11 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float 
 
 // one-time kernel attribute set-up of the sweeps (call before any capture)
 cudaError_t smoother_init();
+// FP32 finest-level sweep vin -> vout with the row-strip kernels;
+// cudaErrorNotSupported when the rows are too long for them
+cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
+                               const float *vin, float *vout, bool descending, cudaStream_t s,
+                               int split);
 // tiled FP32 finest-level sweep vin -> vout (two phase launches); split:
 // the arrays are in parity-split column order
 cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,

@@ -12,10 +12,9 @@
 // same neighbour values), with v read and written about twice per sweep
 // instead of eight times.
 //
-// Two kernels implement the phases.  The finest level, when its rows hold at
-// most 512 nodes, takes the row-strip kernel (k_gs_rows, further below).
-// Otherwise (wider finest rows, and the coarse levels):
-// inside one plane a CTA owns a TX x TY tile and stages a window of that plane
+// The finest level, when its rows hold at most 512 nodes, takes the row-strip
+// kernels of smoother_rows.cu.  Otherwise (wider finest rows, and the coarse
+// levels), inside one plane a CTA owns a TX x TY tile and stages a window of that plane
 // with a halo of HX columns and HY rows in shared memory (17 KB in FP32); the
 // z-neighbour planes and the right-hand side, which the phase only reads,
 // come through the read-only cache.  The same kernel
@@ -360,288 +359,15 @@ cudaError_t sweep(const Dims &d, const Op &op, const T *b, const T *vin, T *vout
 }
 
 
-// ------------------------------------------------------------------------
-// Row-strip phase kernel for the finest level (structured 19-point operator,
-// FP32).  A CTA owns TY whole rows of one plane; thread t owns the node pair
-// x = 2t ("E") and x = 2t+1 ("O") in every row of the strip's window and
-// keeps their values in registers, so of a node's eight in-plane neighbours
-// only the three on the far x side (the neighbouring thread's column) come
-// through shared memory.  Whole rows need no x halo: the periodic x wrap is
-// the neighbour index t-1 / t+1 modulo nx/2.
-//
-// Window rows jj = 0 .. TY+2 are y = y0 - 1 - F + jj.  With the colour order
-// (F,F), (1-F,F), (F,1-F), (1-F,1-F) in (x, y) parity, the F-parity rows are
-// the odd jj and the tile rows are jj = 1+F .. TY+F:
-//   pass 1, 2: x-parity F, then 1-F, on the odd rows 1 .. TY+1 (reading the
-//              old even rows around them);
-//   pass 3, 4: x-parity F, then 1-F, on the even rows 2 .. TY.
-// Every tile node then sees exactly the neighbour values of the sequential
-// colour order; rows 0 and TY+2 are read only.
-//
-// The z-neighbour planes (old values in the first phase, the first phase's
-// output in the second) do not change during a phase, so their contribution
-// is folded into the right-hand side once per node before the passes:
-//   r_c = b_c + z_c,
-//   z_0 = (L0+H0) + kq (D2(x+1) - D2(x-1)),
-//   z_1 = (L1+H1) + kq (D2(y+1) - D2(y-1)),
-//   z_2 = lp (L2+H2) + kq ((D0(x+1) - D0(x-1)) + (D1(y+1) - D1(y-1))),
-// with D = H - L, streamed row by row so each plane value is loaded once.
-constexpr int kRowsMaxThreads = 256;  // rows up to 512 nodes
-
-// update the node of x-parity E at window row jj from the own column values
-// P, the far-side neighbour column X[c][row][tn] (shared) and r
-template <int E, int R>
-__device__ __forceinline__ void rows_update(float (&P)[3][2][R], const float *RS, int t,
-                                            const float *X, int nt, int tn, int jj,
-                                            const Fine<float> &f) {
-    float m[3][3], p[3][3];  // [component][row jj-1, jj, jj+1] at x-1 and x+1
-#pragma unroll
-    for (int q = 0; q < 3; q++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            if (q != 1 && c == 2) continue;  // comp 2 enters only through row jj
-            const float own = P[c][1 - E][jj - 1 + q];
-            const float nb = X[(c * R + jj - 1 + q) * nt + tn];
-            if (E == 0) {
-                p[c][q] = own;
-                m[c][q] = nb;
-            } else {
-                m[c][q] = own;
-                p[c][q] = nb;
-            }
-        }
-    const float lp = f.lp, kq = f.kq, dinv = f.dinv;
-    const float r0 = RS[((0 * 2 + E) * R + jj) * nt + t];
-    const float r1 = RS[((1 * 2 + E) * R + jj) * nt + t];
-    const float r2 = RS[((2 * 2 + E) * R + jj) * nt + t];
-    const float v0 = (r0 + lp * (m[0][1] + p[0][1]) +
-                      (P[0][E][jj - 1] + P[0][E][jj + 1]) +
-                      kq * (p[1][2] - p[1][0] - m[1][2] + m[1][0])) *
-                     dinv;
-    const float v1 = (r1 + lp * (P[1][E][jj - 1] + P[1][E][jj + 1]) +
-                      (m[1][1] + p[1][1]) + kq * (p[0][2] - p[0][0] - m[0][2] + m[0][0])) *
-                     dinv;
-    const float v2 =
-        (r2 + (m[2][1] + p[2][1]) + (P[2][E][jj - 1] + P[2][E][jj + 1])) * dinv;
-    P[0][E][jj] = v0;
-    P[1][E][jj] = v1;
-    P[2][E][jj] = v2;
-}
-
-template <int TY, int F, bool SPLIT>
-__global__ void __launch_bounds__(kRowsMaxThreads, 2)
-    k_gs_rows(Dims d, Fine<float> f, const float *__restrict__ b, const float *__restrict__ vin,
-              const float *__restrict__ zsrc, float *__restrict__ vout, int kbase) {
-    constexpr int R = TY + 3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nt = blockDim.x;
-    float *XE = reinterpret_cast<float *>(smem_raw);  // [3][R][nt] E values by column
-    float *XO = XE + 3 * R * nt;                       // [3][R][nt] O values by column
-    float *RS = XO + 3 * R * nt;                       // [3][2][R][nt] folded right-hand sides
-    const int nx = d.nx, ny = d.ny, hn = nx >> 1;
-    const long ps = (long)nx * ny, cs = d.cs;
-    const int t = threadIdx.x;
-    const bool act = t < hn;
-    const int tc = act ? t : hn - 1;  // spare lanes mirror the last column, store nothing
-    const int tm = tc == 0 ? hn - 1 : tc - 1, tp = tc + 1 == hn ? 0 : tc + 1;
-    const int cE = SPLIT ? tc : 2 * tc, cO = SPLIT ? hn + tc : 2 * tc + 1;
-    const int cOm = SPLIT ? hn + tm : 2 * tm + 1;  // x - 1 of the E node
-    const int cEp = SPLIT ? tp : 2 * tp;           // x + 1 of the O node
-    const int k = 2 * blockIdx.y + kbase;
-    const int y0 = blockIdx.x * TY;
-    const float lp = f.lp, kq = f.kq;
-
-    // right-hand side with the z-neighbour terms folded in, for rows 1 .. R-2,
-    // streamed row by row (row jj's plane values complete row jj-1)
-    const float *Lz = zsrc + (long)(k - 1) * ps, *Hz = zsrc + (long)(k + 1) * ps;
-    const float *Bk = b + (long)k * ps;
-    float S1[3][2], D1[3][2];  // row jj-1: L+H and H-L of the own columns
-    float D2y[2][2];           // row jj-2: H-L of components 1, 2
-    float dm0 = 0.f, dm2 = 0.f, dp0 = 0.f, dp2 = 0.f;  // row jj-1: far-side H-L
-#pragma unroll 2
-    for (int jj = 0; jj < R; jj++) {
-        const int o = wrap_mod(y0 - 1 - F + jj, ny) * nx;
-        float S0[3][2], D0[3][2];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const float lE = __ldg(Lz + c * cs + o + cE), hE = __ldg(Hz + c * cs + o + cE);
-            const float lO = __ldg(Lz + c * cs + o + cO), hO = __ldg(Hz + c * cs + o + cO);
-            S0[c][0] = lE + hE;
-            S0[c][1] = lO + hO;
-            D0[c][0] = hE - lE;
-            D0[c][1] = hO - lO;
-        }
-        const float nm0 = __ldg(Hz + o + cOm) - __ldg(Lz + o + cOm);
-        const float nm2 = __ldg(Hz + 2 * cs + o + cOm) - __ldg(Lz + 2 * cs + o + cOm);
-        const float np0 = __ldg(Hz + o + cEp) - __ldg(Lz + o + cEp);
-        const float np2 = __ldg(Hz + 2 * cs + o + cEp) - __ldg(Lz + 2 * cs + o + cEp);
-        if (jj >= 2) {
-            const int ob = wrap_mod(y0 - 2 - F + jj, ny) * nx;
-            const int w = jj - 1;
-#define RSW(c, e) RS[(((c) * 2 + (e)) * R + w) * nt + t]
-            // E node: x-1 is the neighbour's O column, x+1 the own O column
-            RSW(0, 0) = __ldg(Bk + ob + cE) + (S1[0][0] + kq * (D1[2][1] - dm2));
-            RSW(1, 0) = __ldg(Bk + cs + ob + cE) + (S1[1][0] + kq * (D0[2][0] - D2y[1][0]));
-            RSW(2, 0) = __ldg(Bk + 2 * cs + ob + cE) +
-                        (lp * S1[2][0] + kq * ((D1[0][1] - dm0) + (D0[1][0] - D2y[0][0])));
-            // O node: x-1 is the own E column, x+1 the neighbour's E column
-            RSW(0, 1) = __ldg(Bk + ob + cO) + (S1[0][1] + kq * (dp2 - D1[2][0]));
-            RSW(1, 1) = __ldg(Bk + cs + ob + cO) + (S1[1][1] + kq * (D0[2][1] - D2y[1][1]));
-            RSW(2, 1) = __ldg(Bk + 2 * cs + ob + cO) +
-                        (lp * S1[2][1] + kq * ((dp0 - D1[0][0]) + (D0[1][1] - D2y[0][1])));
-#undef RSW
-        }
-#pragma unroll
-        for (int e = 0; e < 2; e++) {
-            D2y[0][e] = D1[1][e];
-            D2y[1][e] = D1[2][e];
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                S1[c][e] = S0[c][e];
-                D1[c][e] = D0[c][e];
-            }
-        }
-        dm0 = nm0;
-        dm2 = nm2;
-        dp0 = np0;
-        dp2 = np2;
-    }
-
-    // own columns of this plane
-    int roff[R];
-#pragma unroll
-    for (int jj = 0; jj < R; jj++) roff[jj] = wrap_mod(y0 - 1 - F + jj, ny) * nx;
-    const float *Pk = vin + (long)k * ps;
-    float P[3][2][R];
-#pragma unroll
-    for (int c = 0; c < 3; c++)
-#pragma unroll
-        for (int jj = 0; jj < R; jj++) {
-            P[c][0][jj] = __ldg(Pk + c * cs + roff[jj] + cE);
-            P[c][1][jj] = __ldg(Pk + c * cs + roff[jj] + cO);
-        }
-
-    // publish the own columns for the neighbours
-#pragma unroll
-    for (int c = 0; c < 3; c++)
-#pragma unroll
-        for (int jj = 0; jj < R; jj++) {
-            XE[(c * R + jj) * nt + t] = P[c][0][jj];
-            XO[(c * R + jj) * nt + t] = P[c][1][jj];
-        }
-    __syncthreads();
-    // an E node's far side is column t-1's O, an O node's is column t+1's E
-    constexpr int EF = F, EG = 1 - F;
-    float *XF = EF == 0 ? XE : XO, *XG = EG == 0 ? XE : XO;
-    const float *NF = EF == 0 ? XO : XE, *NG = EG == 0 ? XO : XE;
-    const int tnF = EF == 0 ? tm : tp, tnG = EG == 0 ? tm : tp;
-    // pass 1: x-parity F on the odd rows
-#pragma unroll
-    for (int jj = 1; jj < R - 1; jj += 2) {
-        rows_update<EF, R>(P, RS, t, NF, nt, tnF, jj, f);
-#pragma unroll
-        for (int c = 0; c < 3; c++) XF[(c * R + jj) * nt + t] = P[c][EF][jj];
-    }
-    __syncthreads();
-    // pass 2: x-parity 1-F on the odd rows
-#pragma unroll
-    for (int jj = 1; jj < R - 1; jj += 2) {
-        rows_update<EG, R>(P, RS, t, NG, nt, tnG, jj, f);
-#pragma unroll
-        for (int c = 0; c < 3; c++) XG[(c * R + jj) * nt + t] = P[c][EG][jj];
-    }
-    __syncthreads();
-    // pass 3: x-parity F on the even rows
-#pragma unroll
-    for (int jj = 2; jj < R - 2; jj += 2) {
-        rows_update<EF, R>(P, RS, t, NF, nt, tnF, jj, f);
-#pragma unroll
-        for (int c = 0; c < 3; c++) XF[(c * R + jj) * nt + t] = P[c][EF][jj];
-    }
-    __syncthreads();
-    // pass 4: x-parity 1-F on the even rows
-#pragma unroll
-    for (int jj = 2; jj < R - 2; jj += 2) rows_update<EG, R>(P, RS, t, NG, nt, tnG, jj, f);
-
-    // store the tile rows
-    if (!act) return;
-    float *Ok = vout + (long)k * ps;
-#pragma unroll
-    for (int jj = 1 + F; jj < TY + 1 + F; jj++) {
-        const int y = y0 - 1 - F + jj;
-        if (y < ny) {
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                Ok[c * cs + roff[jj] + cE] = P[c][0][jj];
-                Ok[c * cs + roff[jj] + cO] = P[c][1][jj];
-            }
-        }
-    }
-}
-
-constexpr int kRowsTY = 6;  // tile rows: 128 registers without spills
-
-// shared memory of one row-strip CTA: exchange columns (2 x 3 x R) and the
-// folded right-hand sides (3 x 2 x R), nt columns each
-inline size_t rows_smem(int nt) { return 12 * (size_t)(kRowsTY + 3) * nt * sizeof(float); }
-
-template <int F, bool SPLIT>
-cudaError_t launch_rows(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
-                        const float *zsrc, float *vout, int par, cudaStream_t s) {
-    const int kbase = par ? 1 : 2;
-    const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
-    if (nplanes <= 0) return cudaSuccess;
-    const int nt = ((d.nx / 2 + 31) / 32) * 32;
-    const size_t smem = rows_smem(nt);
-    dim3 grid((d.ny + kRowsTY - 1) / kRowsTY, nplanes);
-    k_gs_rows<kRowsTY, F, SPLIT><<<grid, nt, smem, s>>>(d, f, b, vin, zsrc, vout, kbase);
-    count_launch();
-    return cudaGetLastError();
-}
-
-template <int F>
-cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
-                       const float *zsrc, float *vout, int par, cudaStream_t s, int split) {
-    return split ? launch_rows<F, true>(d, f, b, vin, zsrc, vout, par, s)
-                 : launch_rows<F, false>(d, f, b, vin, zsrc, vout, par, s);
-}
-
 }  // namespace
-
-// raise the dynamic shared-memory limit of the row-strip kernels to their
-// largest launch (once, outside any stream capture)
-cudaError_t smoother_init() {
-    const int smem = (int)rows_smem(kRowsMaxThreads);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_gs_rows<kRowsTY, 0, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_gs_rows<kRowsTY, 0, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_gs_rows<kRowsTY, 1, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(k_gs_rows<kRowsTY, 1, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-}
 
 // one 8-colour sweep vin -> vout (vout's wall planes must hold the walls)
 cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,
                                 const float *vin, float *vout, bool descending, cudaStream_t s,
                                 int split) {
-    if (d.nx / 2 <= kRowsMaxThreads) {
-        // whole rows per CTA (row-strip kernel)
-        cudaError_t e;
-        if (!descending) {
-            e = rows_phase<0>(d, f, b, vin, vin, vout, 0, s, split);
-            if (e != cudaSuccess) return e;
-            return rows_phase<0>(d, f, b, vin, vout, vout, 1, s, split);
-        }
-        e = rows_phase<1>(d, f, b, vin, vin, vout, 1, s, split);
-        if (e != cudaSuccess) return e;
-        return rows_phase<1>(d, f, b, vin, vout, vout, 0, s, split);
-    }
+    // whole rows per CTA where the rows are short enough (smoother_rows.cu)
+    const cudaError_t e = gs_sweep_fine_rows(d, f, b, vin, vout, descending, s, split);
+    if (e != cudaErrorNotSupported) return e;
     FineOp<float> op{f};
     return sweep<float>(d, op, b, vin, vout, descending, s, split);
 }

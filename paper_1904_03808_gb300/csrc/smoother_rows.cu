@@ -1,0 +1,572 @@
+// smoother_rows.cu -- row-strip Gauss-Seidel sweep phases for the finest
+// level (structured 19-point operator of the scaled Eq. 30, FP32).
+//
+// One 8-colour sweep runs as two phase launches, as in smoother_fast.cu:
+// the planes of one k-parity (4 in-plane colours each, reading the old
+// z-neighbour planes), then the planes of the other parity (reading the
+// first phase's output).  Here a CTA owns whole rows of a plane, so the
+// periodic x direction needs no halo.  Two kernels:
+//   k_gs_rows_p  persistent (one CTA per SM) for rows of 64, 128 or 256
+//                nodes: the rows of the next tile are copied into shared
+//                memory with cp.async while the current tile computes;
+//   k_gs_rows    one CTA per tile, operands loaded straight into registers,
+//                for the other rows of up to 512 nodes.
+// Both compute every node from the same neighbour values as the sequential
+// colour order (tested against the eight colour launches).
+#include <stdint.h>
+
+#include "qsmg_impl.h"
+
+namespace qsmg {
+namespace {
+
+__device__ __forceinline__ int wrap_mod(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// ------------------------------------------------------------------------
+// Tile geometry shared by both kernels.  A CTA owns TY whole rows of one plane; thread t owns the node pair
+// x = 2t ("E") and x = 2t+1 ("O") in every row of the strip's window and
+// keeps their values in registers, so of a node's eight in-plane neighbours
+// only the three on the far x side (the neighbouring thread's column) come
+// through shared memory.  Whole rows need no x halo: the periodic x wrap is
+// the neighbour index t-1 / t+1 modulo nx/2.
+//
+// Window rows jj = 0 .. TY+2 are y = y0 - 1 - F + jj.  With the colour order
+// (F,F), (1-F,F), (F,1-F), (1-F,1-F) in (x, y) parity, the F-parity rows are
+// the odd jj and the tile rows are jj = 1+F .. TY+F:
+//   pass 1, 2: x-parity F, then 1-F, on the odd rows 1 .. TY+1 (reading the
+//              old even rows around them);
+//   pass 3, 4: x-parity F, then 1-F, on the even rows 2 .. TY.
+// Every tile node then sees exactly the neighbour values of the sequential
+// colour order; rows 0 and TY+2 are read only.
+//
+// The z-neighbour planes (old values in the first phase, the first phase's
+// output in the second) do not change during a phase, so their contribution
+// is folded into the right-hand side once per node before the passes:
+//   r_c = b_c + z_c,
+//   z_0 = (L0+H0) + kq (D2(x+1) - D2(x-1)),
+//   z_1 = (L1+H1) + kq (D2(y+1) - D2(y-1)),
+//   z_2 = lp (L2+H2) + kq ((D0(x+1) - D0(x-1)) + (D1(y+1) - D1(y-1))),
+// with D = H - L, streamed row by row so each plane value is loaded once.
+constexpr int kRowsMaxThreads = 256;  // rows up to 512 nodes
+
+// update the node of x-parity E at window row jj from the own column values
+// P, the far-side neighbour column X[c * sc + row * sr + xn] (shared memory)
+// and the folded right-hand side r
+template <int E, int R>
+__device__ __forceinline__ void rows_update(float (&P)[3][2][R], float r0, float r1, float r2,
+                                            const float *X, int sc, int sr, int xn, int jj,
+                                            const Fine<float> &f) {
+    float m[3][3], p[3][3];  // [component][row jj-1, jj, jj+1] at x-1 and x+1
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            if (q != 1 && c == 2) continue;  // comp 2 enters only through row jj
+            const float own = P[c][1 - E][jj - 1 + q];
+            const float nb = X[c * sc + (jj - 1 + q) * sr + xn];
+            if (E == 0) {
+                p[c][q] = own;
+                m[c][q] = nb;
+            } else {
+                m[c][q] = own;
+                p[c][q] = nb;
+            }
+        }
+    const float lp = f.lp, kq = f.kq, dinv = f.dinv;
+    const float v0 = (r0 + lp * (m[0][1] + p[0][1]) +
+                      (P[0][E][jj - 1] + P[0][E][jj + 1]) +
+                      kq * (p[1][2] - p[1][0] - m[1][2] + m[1][0])) *
+                     dinv;
+    const float v1 = (r1 + lp * (P[1][E][jj - 1] + P[1][E][jj + 1]) +
+                      (m[1][1] + p[1][1]) + kq * (p[0][2] - p[0][0] - m[0][2] + m[0][0])) *
+                     dinv;
+    const float v2 =
+        (r2 + (m[2][1] + p[2][1]) + (P[2][E][jj - 1] + P[2][E][jj + 1])) * dinv;
+    P[0][E][jj] = v0;
+    P[1][E][jj] = v1;
+    P[2][E][jj] = v2;
+}
+
+template <int TY, int F, bool SPLIT>
+__global__ void __launch_bounds__(kRowsMaxThreads, 2)
+    k_gs_rows(Dims d, Fine<float> f, const float *__restrict__ b, const float *__restrict__ vin,
+              const float *__restrict__ zsrc, float *__restrict__ vout, int kbase) {
+    constexpr int R = TY + 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nt = blockDim.x;
+    float *XE = reinterpret_cast<float *>(smem_raw);  // [3][R][nt] E values by column
+    float *XO = XE + 3 * R * nt;                       // [3][R][nt] O values by column
+    float *RS = XO + 3 * R * nt;                       // [3][2][R][nt] folded right-hand sides
+    const int nx = d.nx, ny = d.ny, hn = nx >> 1;
+    const long ps = (long)nx * ny, cs = d.cs;
+    const int t = threadIdx.x;
+    const bool act = t < hn;
+    const int tc = act ? t : hn - 1;  // spare lanes mirror the last column, store nothing
+    const int tm = tc == 0 ? hn - 1 : tc - 1, tp = tc + 1 == hn ? 0 : tc + 1;
+    const int cE = SPLIT ? tc : 2 * tc, cO = SPLIT ? hn + tc : 2 * tc + 1;
+    const int cOm = SPLIT ? hn + tm : 2 * tm + 1;  // x - 1 of the E node
+    const int cEp = SPLIT ? tp : 2 * tp;           // x + 1 of the O node
+    const int k = 2 * blockIdx.y + kbase;
+    const int y0 = blockIdx.x * TY;
+    const float lp = f.lp, kq = f.kq;
+
+    // right-hand side with the z-neighbour terms folded in, for rows 1 .. R-2,
+    // streamed row by row (row jj's plane values complete row jj-1)
+    const float *Lz = zsrc + (long)(k - 1) * ps, *Hz = zsrc + (long)(k + 1) * ps;
+    const float *Bk = b + (long)k * ps;
+    float S1[3][2], D1[3][2];  // row jj-1: L+H and H-L of the own columns
+    float D2y[2][2];           // row jj-2: H-L of components 1, 2
+    float dm0 = 0.f, dm2 = 0.f, dp0 = 0.f, dp2 = 0.f;  // row jj-1: far-side H-L
+#pragma unroll 2
+    for (int jj = 0; jj < R; jj++) {
+        const int o = wrap_mod(y0 - 1 - F + jj, ny) * nx;
+        float S0[3][2], D0[3][2];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float lE = __ldg(Lz + c * cs + o + cE), hE = __ldg(Hz + c * cs + o + cE);
+            const float lO = __ldg(Lz + c * cs + o + cO), hO = __ldg(Hz + c * cs + o + cO);
+            S0[c][0] = lE + hE;
+            S0[c][1] = lO + hO;
+            D0[c][0] = hE - lE;
+            D0[c][1] = hO - lO;
+        }
+        const float nm0 = __ldg(Hz + o + cOm) - __ldg(Lz + o + cOm);
+        const float nm2 = __ldg(Hz + 2 * cs + o + cOm) - __ldg(Lz + 2 * cs + o + cOm);
+        const float np0 = __ldg(Hz + o + cEp) - __ldg(Lz + o + cEp);
+        const float np2 = __ldg(Hz + 2 * cs + o + cEp) - __ldg(Lz + 2 * cs + o + cEp);
+        if (jj >= 2) {
+            const int ob = wrap_mod(y0 - 2 - F + jj, ny) * nx;
+            const int w = jj - 1;
+#define RSW(c, e) RS[(((c) * 2 + (e)) * R + w) * nt + t]
+            // E node: x-1 is the neighbour's O column, x+1 the own O column
+            RSW(0, 0) = __ldg(Bk + ob + cE) + (S1[0][0] + kq * (D1[2][1] - dm2));
+            RSW(1, 0) = __ldg(Bk + cs + ob + cE) + (S1[1][0] + kq * (D0[2][0] - D2y[1][0]));
+            RSW(2, 0) = __ldg(Bk + 2 * cs + ob + cE) +
+                        (lp * S1[2][0] + kq * ((D1[0][1] - dm0) + (D0[1][0] - D2y[0][0])));
+            // O node: x-1 is the own E column, x+1 the neighbour's E column
+            RSW(0, 1) = __ldg(Bk + ob + cO) + (S1[0][1] + kq * (dp2 - D1[2][0]));
+            RSW(1, 1) = __ldg(Bk + cs + ob + cO) + (S1[1][1] + kq * (D0[2][1] - D2y[1][1]));
+            RSW(2, 1) = __ldg(Bk + 2 * cs + ob + cO) +
+                        (lp * S1[2][1] + kq * ((dp0 - D1[0][0]) + (D0[1][1] - D2y[0][1])));
+#undef RSW
+        }
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            D2y[0][e] = D1[1][e];
+            D2y[1][e] = D1[2][e];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                S1[c][e] = S0[c][e];
+                D1[c][e] = D0[c][e];
+            }
+        }
+        dm0 = nm0;
+        dm2 = nm2;
+        dp0 = np0;
+        dp2 = np2;
+    }
+
+    // own columns of this plane
+    int roff[R];
+#pragma unroll
+    for (int jj = 0; jj < R; jj++) roff[jj] = wrap_mod(y0 - 1 - F + jj, ny) * nx;
+    const float *Pk = vin + (long)k * ps;
+    float P[3][2][R];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int jj = 0; jj < R; jj++) {
+            P[c][0][jj] = __ldg(Pk + c * cs + roff[jj] + cE);
+            P[c][1][jj] = __ldg(Pk + c * cs + roff[jj] + cO);
+        }
+
+    // publish the own columns for the neighbours
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int jj = 0; jj < R; jj++) {
+            XE[(c * R + jj) * nt + t] = P[c][0][jj];
+            XO[(c * R + jj) * nt + t] = P[c][1][jj];
+        }
+    __syncthreads();
+    // an E node's far side is column t-1's O, an O node's is column t+1's E
+    constexpr int EF = F, EG = 1 - F;
+    float *XF = EF == 0 ? XE : XO, *XG = EG == 0 ? XE : XO;
+    const float *NF = EF == 0 ? XO : XE, *NG = EG == 0 ? XO : XE;
+    const int tnF = EF == 0 ? tm : tp, tnG = EG == 0 ? tm : tp;
+    // pass 1: x-parity F on the odd rows
+#pragma unroll
+    for (int jj = 1; jj < R - 1; jj += 2) {
+        rows_update<EF, R>(P, RS[((0 * 2 + EF) * R + jj) * nt + t], RS[((1 * 2 + EF) * R + jj) * nt + t],
+                               RS[((2 * 2 + EF) * R + jj) * nt + t], NF, R * nt, nt, tnF, jj, f);
+#pragma unroll
+        for (int c = 0; c < 3; c++) XF[(c * R + jj) * nt + t] = P[c][EF][jj];
+    }
+    __syncthreads();
+    // pass 2: x-parity 1-F on the odd rows
+#pragma unroll
+    for (int jj = 1; jj < R - 1; jj += 2) {
+        rows_update<EG, R>(P, RS[((0 * 2 + EG) * R + jj) * nt + t], RS[((1 * 2 + EG) * R + jj) * nt + t],
+                               RS[((2 * 2 + EG) * R + jj) * nt + t], NG, R * nt, nt, tnG, jj, f);
+#pragma unroll
+        for (int c = 0; c < 3; c++) XG[(c * R + jj) * nt + t] = P[c][EG][jj];
+    }
+    __syncthreads();
+    // pass 3: x-parity F on the even rows
+#pragma unroll
+    for (int jj = 2; jj < R - 2; jj += 2) {
+        rows_update<EF, R>(P, RS[((0 * 2 + EF) * R + jj) * nt + t], RS[((1 * 2 + EF) * R + jj) * nt + t],
+                               RS[((2 * 2 + EF) * R + jj) * nt + t], NF, R * nt, nt, tnF, jj, f);
+#pragma unroll
+        for (int c = 0; c < 3; c++) XF[(c * R + jj) * nt + t] = P[c][EF][jj];
+    }
+    __syncthreads();
+    // pass 4: x-parity 1-F on the even rows
+#pragma unroll
+    for (int jj = 2; jj < R - 2; jj += 2) rows_update<EG, R>(P, RS[((0 * 2 + EG) * R + jj) * nt + t], RS[((1 * 2 + EG) * R + jj) * nt + t],
+                               RS[((2 * 2 + EG) * R + jj) * nt + t], NG, R * nt, nt, tnG, jj, f);
+
+    // store the tile rows
+    if (!act) return;
+    float *Ok = vout + (long)k * ps;
+#pragma unroll
+    for (int jj = 1 + F; jj < TY + 1 + F; jj++) {
+        const int y = y0 - 1 - F + jj;
+        if (y < ny) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                Ok[c * cs + roff[jj] + cE] = P[c][0][jj];
+                Ok[c * cs + roff[jj] + cO] = P[c][1][jj];
+            }
+        }
+    }
+}
+
+constexpr int kRowsTY = 6;  // tile rows: 128 registers without spills
+
+// shared memory of one row-strip CTA: exchange columns (2 x 3 x R) and the
+// folded right-hand sides (3 x 2 x R), nt columns each
+inline size_t rows_smem(int nt) { return 12 * (size_t)(kRowsTY + 3) * nt * sizeof(float); }
+
+template <int F, bool SPLIT>
+cudaError_t launch_rows(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
+                        const float *zsrc, float *vout, int par, cudaStream_t s) {
+    const int kbase = par ? 1 : 2;
+    const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
+    if (nplanes <= 0) return cudaSuccess;
+    const int nt = ((d.nx / 2 + 31) / 32) * 32;
+    const size_t smem = rows_smem(nt);
+    dim3 grid((d.ny + kRowsTY - 1) / kRowsTY, nplanes);
+    k_gs_rows<kRowsTY, F, SPLIT><<<grid, nt, smem, s>>>(d, f, b, vin, zsrc, vout, kbase);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int F>
+cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
+                       const float *zsrc, float *vout, int par, cudaStream_t s, int split) {
+    return split ? launch_rows<F, true>(d, f, b, vin, zsrc, vout, par, s)
+                 : launch_rows<F, false>(d, f, b, vin, zsrc, vout, par, s);
+}
+
+
+// ------------------------------------------------------------------------
+// Persistent kernel.  One CTA per SM walks a contiguous run of the phase's
+// tiles (strip, plane) in strip-major order, so consecutive tiles are
+// consecutive planes of one strip and share a z-neighbour plane (the upper
+// plane of one tile is the lower plane of the next).  What a tile reads --
+// its plane's window rows, its right-hand-side rows and the window rows of
+// the two z-neighbour planes -- is copied into shared memory with 16-byte
+// cp.async copies issued one tile ahead: two stages for the plane and
+// right-hand-side rows, four slots for z-neighbour planes (two in use, two
+// filling), so the copies of tile i+1 run while tile i computes.  Shared
+// rows are laid out [row][component][nx] in the arrays' own column order;
+// the stage's plane rows are updated in place and serve as the exchange
+// buffer of the passes.  Copy lanes: thread t moves 16-byte chunk t % (nx/4)
+// of the rows of parity t / (nx/4) (blockDim = nx/2 = 2 * nx/4).
+constexpr int kPersTY = 6;
+constexpr int kPersR = kPersTY + 3;
+constexpr int kPersZSlots = 4;
+constexpr int kPersMaxNx = 256;
+
+__host__ __device__ constexpr long pers_floats(int nx) {
+    return (long)(2 * 3 * kPersR + 2 * 3 * (kPersR - 2) + kPersZSlots * 3 * kPersR) * nx;
+}
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int F, bool SPLIT>
+__global__ void __launch_bounds__(kPersMaxNx / 2, 1)
+    k_gs_rows_p(Dims d, Fine<float> f, const float *__restrict__ b, const float *__restrict__ vin,
+                const float *__restrict__ zsrc, float *__restrict__ vout, int kbase, int nplanes,
+                int nstrips) {
+    constexpr int TY = kPersTY, R = kPersR;
+    extern __shared__ __align__(16) float sm[];
+    const int nx = d.nx, ny = d.ny, hn = nx >> 1, cpr = nx >> 2;
+    const long ps = (long)nx * ny, cs = d.cs;
+    const int plane_f = 3 * R * nx, bst_f = 3 * (R - 2) * nx;
+    float *const Pst0 = sm, *const Bst0 = sm + 2 * plane_f, *const Zs0 = Bst0 + 2 * bst_f;
+    const int t = threadIdx.x;
+    const int q4 = 4 * (t % cpr), g = t / cpr;
+    const int tm = t == 0 ? hn - 1 : t - 1, tp = t + 1 == hn ? 0 : t + 1;
+    const int xe = SPLIT ? t : 2 * t, xo = SPLIT ? hn + t : 2 * t + 1;
+    const int xom = SPLIT ? hn + tm : 2 * tm + 1;  // x - 1 of the E node
+    const int xep = SPLIT ? tp : 2 * tp;           // x + 1 of the O node
+    const long ntiles = (long)nstrips * nplanes;
+    const long n0 = blockIdx.x * ntiles / gridDim.x, n1 = (blockIdx.x + 1) * ntiles / gridDim.x;
+    if (n0 >= n1) return;
+
+    // window rows [jlo, jhi) of plane q of src into dst (rows from jlo)
+    auto copy_rows = [&](float *dst, const float *src, int q, int y0, int jlo, int jhi) {
+        const float *base = src + (long)q * ps + q4;
+        for (int jj = jlo + g; jj < jhi; jj += 2) {
+            int y = y0 - 1 - F + jj;  // ny >= R: at most one wrap
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            const float *srow = base + (long)y * nx;
+            float *drow = dst + (jj - jlo) * 3 * nx + q4;
+            cp_async16(drow, srow);
+            cp_async16(drow + nx, srow + cs);
+            cp_async16(drow + 2 * nx, srow + 2 * cs);
+        }
+    };
+    // z-plane slots: tag = strip * (nz + 1) + plane, uniform over the CTA
+    int tag[kPersZSlots];
+#pragma unroll
+    for (int i = 0; i < kPersZSlots; i++) tag[i] = -1;
+    auto find = [&](int key) {
+        int s = -1;
+#pragma unroll
+        for (int i = 0; i < kPersZSlots; i++)
+            if (tag[i] == key) s = i;
+        return s;
+    };
+    auto take = [&](int key, int u0, int u1, int u2) {
+        int s = -1;
+#pragma unroll
+        for (int i = kPersZSlots - 1; i >= 0; i--)
+            if (i != u0 && i != u1 && i != u2) s = i;
+#pragma unroll
+        for (int i = 0; i < kPersZSlots; i++)
+            if (i == s) tag[i] = key;
+        return s;
+    };
+    // issue the copies of tile n into stage st; slots in use: cu0, cu1
+    auto issue = [&](long n, int st, int cu0, int cu1, int &sL, int &sH) {
+        const int s = (int)(n / nplanes), k = 2 * (int)(n - (long)s * nplanes) + kbase;
+        const int y0 = s * TY;
+        copy_rows(Pst0 + st * plane_f, vin, k, y0, 0, R);
+        copy_rows(Bst0 + st * bst_f, b, k, y0, 1, R - 1);
+        const int keyL = s * (d.nz + 1) + k - 1, keyH = keyL + 2;
+        sL = find(keyL);
+        if (sL < 0) {
+            sL = take(keyL, cu0, cu1, -1);
+            copy_rows(Zs0 + sL * plane_f, zsrc, k - 1, y0, 0, R);
+        }
+        sH = find(keyH);
+        if (sH < 0) {
+            sH = take(keyH, cu0, cu1, sL);
+            copy_rows(Zs0 + sH * plane_f, zsrc, k + 1, y0, 0, R);
+        }
+        cp_async_commit();
+    };
+
+    const float lp = f.lp, kq = f.kq;
+    int sL, sH, stage = 0;
+    issue(n0, 0, -1, -1, sL, sH);
+    for (long n = n0; n < n1; n++) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int cL = sL, cH = sH;
+        if (n + 1 < n1) issue(n + 1, stage ^ 1, cL, cH, sL, sH);
+        const int s = (int)(n / nplanes), k = 2 * (int)(n - (long)s * nplanes) + kbase;
+        const int y0 = s * TY;
+        float *Ps = Pst0 + stage * plane_f;
+        const float *Bs = Bst0 + stage * bst_f;
+        const float *Ls = Zs0 + cL * plane_f, *Hs = Zs0 + cH * plane_f;
+#define AT(row, c, x) ((((row) * 3) + (c)) * nx + (x))
+#define DZ(row, c, x) (Hs[AT(row, c, x)] - Ls[AT(row, c, x)])
+#define SZ(row, c, x) (Hs[AT(row, c, x)] + Ls[AT(row, c, x)])
+        // right-hand side with the z-neighbour terms folded in
+        float r[3][2][R];
+#pragma unroll
+        for (int jj = 1; jj < R - 1; jj++) {
+            const float dOm0 = DZ(jj, 0, xom), dOm2 = DZ(jj, 2, xom);
+            const float dEp0 = DZ(jj, 0, xep), dEp2 = DZ(jj, 2, xep);
+            const float dE0 = DZ(jj, 0, xe), dE2 = DZ(jj, 2, xe);
+            const float dO0 = DZ(jj, 0, xo), dO2 = DZ(jj, 2, xo);
+            // E node: x-1 is the neighbour's O column, x+1 the own O column
+            r[0][0][jj] = Bs[AT(jj - 1, 0, xe)] + (SZ(jj, 0, xe) + kq * (dO2 - dOm2));
+            r[1][0][jj] = Bs[AT(jj - 1, 1, xe)] +
+                          (SZ(jj, 1, xe) + kq * (DZ(jj + 1, 2, xe) - DZ(jj - 1, 2, xe)));
+            r[2][0][jj] = Bs[AT(jj - 1, 2, xe)] +
+                          (lp * SZ(jj, 2, xe) +
+                           kq * ((dO0 - dOm0) + (DZ(jj + 1, 1, xe) - DZ(jj - 1, 1, xe))));
+            // O node: x-1 is the own E column, x+1 the neighbour's E column
+            r[0][1][jj] = Bs[AT(jj - 1, 0, xo)] + (SZ(jj, 0, xo) + kq * (dEp2 - dE2));
+            r[1][1][jj] = Bs[AT(jj - 1, 1, xo)] +
+                          (SZ(jj, 1, xo) + kq * (DZ(jj + 1, 2, xo) - DZ(jj - 1, 2, xo)));
+            r[2][1][jj] = Bs[AT(jj - 1, 2, xo)] +
+                          (lp * SZ(jj, 2, xo) +
+                           kq * ((dEp0 - dE0) + (DZ(jj + 1, 1, xo) - DZ(jj - 1, 1, xo))));
+        }
+#undef DZ
+#undef SZ
+        float P[3][2][R];
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int jj = 0; jj < R; jj++) {
+                P[c][0][jj] = Ps[AT(jj, c, xe)];
+                P[c][1][jj] = Ps[AT(jj, c, xo)];
+            }
+        constexpr int EF = F, EG = 1 - F;
+        const int xF = EF == 0 ? xe : xo, xG = EG == 0 ? xe : xo;
+        const int nF = EF == 0 ? xom : xep, nG = EG == 0 ? xom : xep;
+        // pass 1: x-parity F on the odd rows
+#pragma unroll
+        for (int jj = 1; jj < R - 1; jj += 2) {
+            rows_update<EF, R>(P, r[0][EF][jj], r[1][EF][jj], r[2][EF][jj], Ps, nx, 3 * nx, nF,
+                               jj, f);
+#pragma unroll
+            for (int c = 0; c < 3; c++) Ps[AT(jj, c, xF)] = P[c][EF][jj];
+        }
+        __syncthreads();
+        // pass 2: x-parity 1-F on the odd rows
+#pragma unroll
+        for (int jj = 1; jj < R - 1; jj += 2) {
+            rows_update<EG, R>(P, r[0][EG][jj], r[1][EG][jj], r[2][EG][jj], Ps, nx, 3 * nx, nG,
+                               jj, f);
+#pragma unroll
+            for (int c = 0; c < 3; c++) Ps[AT(jj, c, xG)] = P[c][EG][jj];
+        }
+        __syncthreads();
+        // pass 3: x-parity F on the even rows
+#pragma unroll
+        for (int jj = 2; jj < R - 2; jj += 2) {
+            rows_update<EF, R>(P, r[0][EF][jj], r[1][EF][jj], r[2][EF][jj], Ps, nx, 3 * nx, nF,
+                               jj, f);
+#pragma unroll
+            for (int c = 0; c < 3; c++) Ps[AT(jj, c, xF)] = P[c][EF][jj];
+        }
+        __syncthreads();
+        // pass 4: x-parity 1-F on the even rows
+#pragma unroll
+        for (int jj = 2; jj < R - 2; jj += 2)
+            rows_update<EG, R>(P, r[0][EG][jj], r[1][EG][jj], r[2][EG][jj], Ps, nx, 3 * nx, nG,
+                               jj, f);
+#undef AT
+        // store the tile rows
+        float *Ok = vout + (long)k * ps;
+#pragma unroll
+        for (int jj = 1 + F; jj < TY + 1 + F; jj++) {
+            const int y = y0 - 1 - F + jj;
+            if (y < ny) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    Ok[c * cs + (long)y * nx + xe] = P[c][0][jj];
+                    Ok[c * cs + (long)y * nx + xo] = P[c][1][jj];
+                }
+            }
+        }
+        stage ^= 1;
+    }
+}
+
+int g_sms[64];  // SM count per device, set by smoother_init
+
+template <int F, bool SPLIT>
+cudaError_t launch_rows_p(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
+                          const float *zsrc, float *vout, int par, cudaStream_t s, int sms) {
+    const int kbase = par ? 1 : 2;
+    const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
+    if (nplanes <= 0) return cudaSuccess;
+    const int nstrips = (d.ny + kPersTY - 1) / kPersTY;
+    const long ntiles = (long)nstrips * nplanes;
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    k_gs_rows_p<F, SPLIT><<<grid, d.nx / 2, pers_floats(d.nx) * sizeof(float), s>>>(
+        d, f, b, vin, zsrc, vout, kbase, nplanes, nstrips);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int F>
+cudaError_t rows_p_phase(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
+                         const float *zsrc, float *vout, int par, cudaStream_t s, int split,
+                         int sms) {
+    return split ? launch_rows_p<F, true>(d, f, b, vin, zsrc, vout, par, s, sms)
+                 : launch_rows_p<F, false>(d, f, b, vin, zsrc, vout, par, s, sms);
+}
+
+}  // namespace
+
+cudaError_t smoother_init() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) {
+        e = cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    const int smem = (int)rows_smem(kRowsMaxThreads);
+    const int smem_p = (int)(pers_floats(kPersMaxNx) * sizeof(float));
+#define SET(kern, bytes)                                                                   \
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != \
+        cudaSuccess)                                                                       \
+        return e;
+    SET((k_gs_rows<kRowsTY, 0, false>), smem)
+    SET((k_gs_rows<kRowsTY, 0, true>), smem)
+    SET((k_gs_rows<kRowsTY, 1, false>), smem)
+    SET((k_gs_rows<kRowsTY, 1, true>), smem)
+    SET((k_gs_rows_p<0, false>), smem_p)
+    SET((k_gs_rows_p<0, true>), smem_p)
+    SET((k_gs_rows_p<1, false>), smem_p)
+    SET((k_gs_rows_p<1, true>), smem_p)
+#undef SET
+    return cudaSuccess;
+}
+
+// one 8-colour sweep vin -> vout with the row-strip kernels, or
+// cudaErrorNotSupported if the rows are too long for them
+cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
+                               const float *vin, float *vout, bool descending, cudaStream_t s,
+                               int split) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int sms = (dev >= 0 && dev < 64) ? g_sms[dev] : 0;
+    const bool aligned =
+        (((uintptr_t)b | (uintptr_t)vin | (uintptr_t)vout) & 15) == 0;
+    if (sms > 0 && aligned && d.nx % 64 == 0 && d.nx <= kPersMaxNx && d.ny >= kPersR) {
+        if (!descending) {
+            e = rows_p_phase<0>(d, f, b, vin, vin, vout, 0, s, split, sms);
+            if (e != cudaSuccess) return e;
+            return rows_p_phase<0>(d, f, b, vin, vout, vout, 1, s, split, sms);
+        }
+        e = rows_p_phase<1>(d, f, b, vin, vin, vout, 1, s, split, sms);
+        if (e != cudaSuccess) return e;
+        return rows_p_phase<1>(d, f, b, vin, vout, vout, 0, s, split, sms);
+    }
+    if (d.nx / 2 > kRowsMaxThreads) return cudaErrorNotSupported;
+    if (!descending) {
+        e = rows_phase<0>(d, f, b, vin, vin, vout, 0, s, split);
+        if (e != cudaSuccess) return e;
+        return rows_phase<0>(d, f, b, vin, vout, vout, 1, s, split);
+    }
+    e = rows_phase<1>(d, f, b, vin, vin, vout, 1, s, split);
+    if (e != cudaSuccess) return e;
+    return rows_phase<1>(d, f, b, vin, vout, vout, 0, s, split);
+}
+
+}  // namespace qsmg

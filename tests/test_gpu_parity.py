@@ -118,13 +118,15 @@ def test_smoother_fp32_fine_level(shape):
 
 
 @pytest.mark.parametrize("shape", [(72, 40, 16), (16, 8, 12), (8, 4, 2), (136, 72, 32), (64, 32, 32),
-                                   (10, 16, 16), (1024, 64, 64)])
+                                   (10, 16, 16), (1024, 64, 64), (256, 32, 32), (128, 40, 32)])
 @pytest.mark.parametrize("sweeps,descending", [(1, False), (2, False), (1, True), (3, True)])
 def test_tiled_fp32_sweep_equals_colour_passes(shape, sweeps, descending):
     """The tiled two-phase FP32 sweeps reproduce the eight colour launches on
     every smoothed level (ragged tiles, odd sweep counts, non-zero walls on the
-    finest level, both colour orders); rows of up to 512 nodes take the
-    row-strip kernel on the finest level, wider rows (1024) the tile kernel."""
+    finest level, both colour orders).  On the finest level rows of 64, 128
+    and 256 nodes take the persistent row-strip kernel, other rows of up to
+    512 nodes the per-tile row-strip kernel, wider rows (1024) the tile
+    kernel."""
     rng = np.random.default_rng(7)
     ctxs = [ctx_for(shape, precision=MG_MIXED, flags=f) for f in (0, 1)]
     nlev = ctxs[0].levels
