@@ -274,19 +274,21 @@ cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, cons
 
 
 // ------------------------------------------------------------------------
-// Persistent kernel.  One CTA per SM walks a contiguous run of the phase's
-// tiles (strip, plane) in strip-major order, so consecutive tiles are
-// consecutive planes of one strip and share a z-neighbour plane (the upper
-// plane of one tile is the lower plane of the next).  What a tile reads --
-// its plane's window rows, its right-hand-side rows and the window rows of
-// the two z-neighbour planes -- is copied into shared memory with 16-byte
-// cp.async copies issued one tile ahead: two stages for the plane and
-// right-hand-side rows, four slots for z-neighbour planes (two in use, two
-// filling), so the copies of tile i+1 run while tile i computes.  Shared
-// rows are laid out [row][component][nx] in the arrays' own column order;
-// the stage's plane rows are updated in place and serve as the exchange
-// buffer of the passes.  Copy lanes: thread t moves 16-byte chunk t % (nx/4)
-// of the rows of parity t / (nx/4) (blockDim = nx/2 = 2 * nx/4).
+// Persistent kernel.  One CTA per SM takes every gridDim.x-th tile of the
+// phase in plane-major order (tile n: plane n / nstrips, strip n % nstrips),
+// so at any moment the whole GPU works on a band of about four planes and the
+// window rows that neighbouring strips and planes share are still in L2 when
+// the second reader asks for them.  What a tile reads -- its plane's window
+// rows, its right-hand-side rows and the window rows of the two z-neighbour
+// planes -- is copied into shared memory with 16-byte cp.async copies issued
+// one tile ahead (two stages for the plane and right-hand-side rows, four
+// slots for z-neighbour planes: two in use, two filling; a slot already
+// holding a needed plane is reused), so the copies of the next tile run while
+// the current one computes.  Shared rows are laid out [row][component][nx]
+// in the arrays' own column order; the stage's plane rows are updated in
+// place and serve as the exchange buffer of the passes.  Copy lanes: thread t
+// moves 16-byte chunk t % (nx/4) of the rows of parity t / (nx/4)
+// (blockDim = nx/2 = 2 * nx/4).
 constexpr int kPersTY = 6;
 constexpr int kPersR = kPersTY + 3;
 constexpr int kPersZSlots = 4;
@@ -325,8 +327,7 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, 1)
     const int xom = SPLIT ? hn + tm : 2 * tm + 1;  // x - 1 of the E node
     const int xep = SPLIT ? tp : 2 * tp;           // x + 1 of the O node
     const long ntiles = (long)nstrips * nplanes;
-    const long n0 = blockIdx.x * ntiles / gridDim.x, n1 = (blockIdx.x + 1) * ntiles / gridDim.x;
-    if (n0 >= n1) return;
+    if ((long)blockIdx.x >= ntiles) return;
 
     // window rows [jlo, jhi) of plane q of src into dst (rows from jlo)
     auto copy_rows = [&](float *dst, const float *src, int q, int y0, int jlo, int jhi) {
@@ -364,8 +365,8 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, 1)
     };
     // issue the copies of tile n into stage st; slots in use: cu0, cu1
     auto issue = [&](long n, int st, int cu0, int cu1, int &sL, int &sH) {
-        const int s = (int)(n / nplanes), k = 2 * (int)(n - (long)s * nplanes) + kbase;
-        const int y0 = s * TY;
+        const int p = (int)(n / nstrips), s = (int)(n - (long)p * nstrips);
+        const int k = 2 * p + kbase, y0 = s * TY;
         copy_rows(Pst0 + st * plane_f, vin, k, y0, 0, R);
         copy_rows(Bst0 + st * bst_f, b, k, y0, 1, R - 1);
         const int keyL = s * (d.nz + 1) + k - 1, keyH = keyL + 2;
@@ -384,14 +385,15 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, 1)
 
     const float lp = f.lp, kq = f.kq;
     int sL, sH, stage = 0;
-    issue(n0, 0, -1, -1, sL, sH);
-    for (long n = n0; n < n1; n++) {
+    const long step = gridDim.x;
+    issue(blockIdx.x, 0, -1, -1, sL, sH);
+    for (long n = blockIdx.x; n < ntiles; n += step) {
         cp_async_wait_all();
         __syncthreads();
         const int cL = sL, cH = sH;
-        if (n + 1 < n1) issue(n + 1, stage ^ 1, cL, cH, sL, sH);
-        const int s = (int)(n / nplanes), k = 2 * (int)(n - (long)s * nplanes) + kbase;
-        const int y0 = s * TY;
+        if (n + step < ntiles) issue(n + step, stage ^ 1, cL, cH, sL, sH);
+        const int p = (int)(n / nstrips), s = (int)(n - (long)p * nstrips);
+        const int k = 2 * p + kbase, y0 = s * TY;
         float *Ps = Pst0 + stage * plane_f;
         const float *Bs = Bst0 + stage * bst_f;
         const float *Ls = Zs0 + cL * plane_f, *Hs = Zs0 + cH * plane_f;
