@@ -72,9 +72,12 @@ def run_sweeps(args):
     for _ in range(max(args.warmup, 3)):
         ctx.smooth(0, b, x, 2, False)
     ctx.profile(True)
+    clocks = Clocks(0)
+    clocks.start()
     for _ in range(args.steps):
         ctx.smooth(0, b, x, 2, False)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     sm_ms, sweeps, launches = ctx.profile_read()
     ctx.profile(False)
     ctx.close()
@@ -82,7 +85,7 @@ def run_sweeps(args):
     nodes = n * n * (nz - 1)
     return {"mode": "sweep-only", "grid": [n, n, nz], "sweeps": sweeps, "sweep_ms": t,
             "achieved_gbs": SMOOTH_BYTES * nodes / (t / 1e3) / 1e9,
-            "launches_per_sweep": launches / max(sweeps, 1)}
+            "launches_per_sweep": launches / max(sweeps, 1), "clocks": clk}
 
 
 def workload(n):

@@ -274,28 +274,36 @@ cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, cons
 
 
 // ------------------------------------------------------------------------
-// Persistent kernel.  One CTA per SM takes every gridDim.x-th tile of the
-// phase in plane-major order (tile n: plane n / nstrips, strip n % nstrips),
-// so at any moment the whole GPU works on a band of about four planes and the
-// window rows that neighbouring strips and planes share are still in L2 when
-// the second reader asks for them.  What a tile reads -- its plane's window
-// rows, its right-hand-side rows and the window rows of the two z-neighbour
-// planes -- is copied into shared memory with 16-byte cp.async copies issued
-// one tile ahead (two stages for the plane and right-hand-side rows, four
-// slots for z-neighbour planes: two in use, two filling; a slot already
-// holding a needed plane is reused), so the copies of the next tile run while
-// the current one computes.  Shared rows are laid out [row][component][nx]
-// in the arrays' own column order; the stage's plane rows are updated in
-// place and serve as the exchange buffer of the passes.  Copy lanes: thread t
-// moves 16-byte chunk t % (nx/4) of the rows of parity t / (nx/4)
-// (blockDim = nx/2 = 2 * nx/4).
+// Persistent kernel.  Two CTAs per SM (128 threads each at nx = 256), each
+// walking a contiguous run of the phase's tiles (strip, plane).  Tiles are
+// ordered by blocks of kPersPB planes, then strip, then plane: consecutive
+// tiles are mostly consecutive planes of one strip and share a z-neighbour
+// plane (the upper plane of one tile is the lower plane of the next), and
+// neighbouring strips reach the same plane within a few tiles, so the window
+// rows they share are still in L2.  A tile's operands -- its plane's window
+// rows, its right-hand-side rows and the window rows of its two z-neighbour
+// planes -- are copied into shared memory with 16-byte cp.async copies
+// issued when the previous tile is done (a z-plane slot already holding a
+// needed plane is kept); the other CTA on the SM computes while they land.
+// Shared rows are laid out [row][component][nx] in the arrays' own column
+// order; the plane rows are updated in place and serve as the exchange
+// buffer of the passes.  Copy lanes: thread t moves 16-byte chunk t % (nx/4)
+// of the rows of parity t / (nx/4) (blockDim = nx/2 = 2 * nx/4).
+// Measured on GB300 and dropped: one CTA per SM with double-buffered stages
+// and four z-plane slots (24% slower); issuing the next tile's right-hand
+// side and z-plane copies right after the first pass, when they are dead
+// (6% slower); a cyclic plane-major tile order (27%
+// fewer DRAM bytes, 18% slower: it loses the z-plane reuse); one thread per
+// node component instead of per column pair (35% slower); natural instead of
+// parity-split column order (8% slower).
 constexpr int kPersTY = 6;
 constexpr int kPersR = kPersTY + 3;
-constexpr int kPersZSlots = 4;
+constexpr int kPersMinBlocks = 2;  // resident CTAs per SM
 constexpr int kPersMaxNx = 256;
+constexpr int kPersPB = 16;  // planes per block of the tile order
 
 __host__ __device__ constexpr long pers_floats(int nx) {
-    return (long)(2 * 3 * kPersR + 2 * 3 * (kPersR - 2) + kPersZSlots * 3 * kPersR) * nx;
+    return (long)(3 * kPersR + 3 * (kPersR - 2) + 2 * 3 * kPersR) * nx;
 }
 
 __device__ __forceinline__ void cp_async16(float *dst, const float *src) {
@@ -310,7 +318,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 template <int F, bool SPLIT>
-__global__ void __launch_bounds__(kPersMaxNx / 2, 1)
+__global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
     k_gs_rows_p(Dims d, Fine<float> f, const float *__restrict__ b, const float *__restrict__ vin,
                 const float *__restrict__ zsrc, float *__restrict__ vout, int kbase, int nplanes,
                 int nstrips) {
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, 1)
     const int nx = d.nx, ny = d.ny, hn = nx >> 1, cpr = nx >> 2;
     const long ps = (long)nx * ny, cs = d.cs;
     const int plane_f = 3 * R * nx, bst_f = 3 * (R - 2) * nx;
-    float *const Pst0 = sm, *const Bst0 = sm + 2 * plane_f, *const Zs0 = Bst0 + 2 * bst_f;
+    float *const Ps = sm, *const Bs = sm + plane_f, *const Zs0 = Bs + bst_f;
     const int t = threadIdx.x;
     const int q4 = 4 * (t % cpr), g = t / cpr;
     const int tm = t == 0 ? hn - 1 : t - 1, tp = t + 1 == hn ? 0 : t + 1;
@@ -327,7 +335,8 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, 1)
     const int xom = SPLIT ? hn + tm : 2 * tm + 1;  // x - 1 of the E node
     const int xep = SPLIT ? tp : 2 * tp;           // x + 1 of the O node
     const long ntiles = (long)nstrips * nplanes;
-    if ((long)blockIdx.x >= ntiles) return;
+    const long n0 = blockIdx.x * ntiles / gridDim.x, n1 = (blockIdx.x + 1) * ntiles / gridDim.x;
+    if (n0 >= n1) return;
 
     // window rows [jlo, jhi) of plane q of src into dst (rows from jlo)
     auto copy_rows = [&](float *dst, const float *src, int q, int y0, int jlo, int jhi) {
@@ -342,60 +351,63 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, 1)
             cp_async16(drow + 2 * nx, srow + 2 * cs);
         }
     };
-    // z-plane slots: tag = strip * (nz + 1) + plane, uniform over the CTA
-    int tag[kPersZSlots];
-#pragma unroll
-    for (int i = 0; i < kPersZSlots; i++) tag[i] = -1;
-    auto find = [&](int key) {
-        int s = -1;
-#pragma unroll
-        for (int i = 0; i < kPersZSlots; i++)
-            if (tag[i] == key) s = i;
-        return s;
+    // tile n -> strip s, plane k
+    auto tile_of = [&](long n, int &s, int &k) {
+        const int blk = (int)(n / ((long)nstrips * kPersPB));
+        const int pb = nplanes - blk * kPersPB < kPersPB ? nplanes - blk * kPersPB : kPersPB;
+        const int rem = (int)(n - (long)blk * nstrips * kPersPB);
+        s = rem / pb;
+        k = 2 * (blk * kPersPB + rem - s * pb) + kbase;
     };
-    auto take = [&](int key, int u0, int u1, int u2) {
-        int s = -1;
-#pragma unroll
-        for (int i = kPersZSlots - 1; i >= 0; i--)
-            if (i != u0 && i != u1 && i != u2) s = i;
-#pragma unroll
-        for (int i = 0; i < kPersZSlots; i++)
-            if (i == s) tag[i] = key;
-        return s;
-    };
-    // issue the copies of tile n into stage st; slots in use: cu0, cu1
-    auto issue = [&](long n, int st, int cu0, int cu1, int &sL, int &sH) {
-        const int p = (int)(n / nstrips), s = (int)(n - (long)p * nstrips);
-        const int k = 2 * p + kbase, y0 = s * TY;
-        copy_rows(Pst0 + st * plane_f, vin, k, y0, 0, R);
-        copy_rows(Bst0 + st * bst_f, b, k, y0, 1, R - 1);
+    // z-plane slots 0, 1 (tag: strip * (nz + 1) + plane; uniform over the CTA)
+    int tag0 = -1, tag1 = -1;
+    // right-hand-side rows and z-neighbour planes of tile n (a slot holding a
+    // needed plane is kept, the other one refilled)
+    auto issue_bz = [&](long n, int &sL, int &sH) {
+        int s, k;
+        tile_of(n, s, k);
+        const int y0 = s * TY;
+        copy_rows(Bs, b, k, y0, 1, R - 1);
         const int keyL = s * (d.nz + 1) + k - 1, keyH = keyL + 2;
-        sL = find(keyL);
+        sL = tag0 == keyL ? 0 : (tag1 == keyL ? 1 : -1);
+        sH = tag0 == keyH ? 0 : (tag1 == keyH ? 1 : -1);
         if (sL < 0) {
-            sL = take(keyL, cu0, cu1, -1);
+            sL = sH == 0 ? 1 : 0;
+            if (sL == 0)
+                tag0 = keyL;
+            else
+                tag1 = keyL;
             copy_rows(Zs0 + sL * plane_f, zsrc, k - 1, y0, 0, R);
         }
-        sH = find(keyH);
         if (sH < 0) {
-            sH = take(keyH, cu0, cu1, sL);
+            sH = 1 - sL;
+            if (sH == 0)
+                tag0 = keyH;
+            else
+                tag1 = keyH;
             copy_rows(Zs0 + sH * plane_f, zsrc, k + 1, y0, 0, R);
         }
         cp_async_commit();
     };
+    // plane rows of tile n
+    auto issue_p = [&](long n) {
+        int s, k;
+        tile_of(n, s, k);
+        copy_rows(Ps, vin, k, s * TY, 0, R);
+        cp_async_commit();
+    };
 
     const float lp = f.lp, kq = f.kq;
-    int sL, sH, stage = 0;
-    const long step = gridDim.x;
-    issue(blockIdx.x, 0, -1, -1, sL, sH);
-    for (long n = blockIdx.x; n < ntiles; n += step) {
+    int sL, sH;
+    issue_bz(n0, sL, sH);
+    issue_p(n0);
+    for (long n = n0; n < n1; n++) {
         cp_async_wait_all();
         __syncthreads();
         const int cL = sL, cH = sH;
-        if (n + step < ntiles) issue(n + step, stage ^ 1, cL, cH, sL, sH);
-        const int p = (int)(n / nstrips), s = (int)(n - (long)p * nstrips);
-        const int k = 2 * p + kbase, y0 = s * TY;
-        float *Ps = Pst0 + stage * plane_f;
-        const float *Bs = Bst0 + stage * bst_f;
+        int s, k;
+        tile_of(n, s, k);
+        const int y0 = s * TY;
         const float *Ls = Zs0 + cL * plane_f, *Hs = Zs0 + cH * plane_f;
 #define AT(row, c, x) ((((row) * 3) + (c)) * nx + (x))
 #define DZ(row, c, x) (Hs[AT(row, c, x)] - Ls[AT(row, c, x)])
@@ -482,7 +494,12 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, 1)
                 }
             }
         }
-        stage ^= 1;
+        if (n + 1 < n1) {
+            // refill once every thread is done with this tile
+            __syncthreads();
+            issue_bz(n + 1, sL, sH);
+            issue_p(n + 1);
+        }
     }
 }
 
@@ -496,7 +513,8 @@ cudaError_t launch_rows_p(const Dims &d, const Fine<float> &f, const float *b, c
     if (nplanes <= 0) return cudaSuccess;
     const int nstrips = (d.ny + kPersTY - 1) / kPersTY;
     const long ntiles = (long)nstrips * nplanes;
-    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    const long slots = (long)sms * kPersMinBlocks;
+    const int grid = (int)(ntiles < slots ? ntiles : slots);
     k_gs_rows_p<F, SPLIT><<<grid, d.nx / 2, pers_floats(d.nx) * sizeof(float), s>>>(
         d, f, b, vin, zsrc, vout, kbase, nplanes, nstrips);
     count_launch();
