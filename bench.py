@@ -15,6 +15,13 @@ Prints one JSON line (rank 0).
         python bench.py --sweep-only [--n N] [--nz NZ] [--steps K]
 times K finest-level FP32 sweeps alone (two per call, random data, one GPU)
 and prints their mean duration; the small case for kernel profiles.
+
+        python bench.py --disc [--n 512] [--steps 20]
+friction-welding disc workload (section 5): n^3 cells, bottom wall fixed, top
+wall rotating inside radius R = L/3 (omega = 2 pi / (1e8 t_s)), dt = 2e4 t_s,
+chi0 with correlation length 8 cells; mixed and FP64 run in lockstep from the
+same state; per-step device times and the mixed run's velocity and stress
+error against the FP64 run.
 """
 from __future__ import annotations
 
@@ -47,12 +54,92 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--inner", type=int, default=INNER)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-only", action="store_true")
+    ap.add_argument("--disc", action="store_true")
+    ap.add_argument("--dt-ts", type=float, default=2.0e4)
+    ap.add_argument("--chi", default="450,15,5",
+                    help="disc chi0 recipe: mean K, std K, correlation length in cells")
     ap.add_argument("--nz", type=int, default=0)
     return ap.parse_args()
+
+
+def run_disc(args):
+    """Disc-rotation workload, mixed and FP64 in lockstep (one GPU)."""
+    import math
+
+    import torch
+
+    from paper_1904_03808_gb300 import MG_FP64, MG_MIXED, Context, make_state
+    from paper_1904_03808_gb300 import inputs as I
+    n = args.n or 512
+    K = args.steps
+    cm, cs_, clc = (float(x) for x in args.chi.split(","))
+    t_setup = time.time()
+    w = I.Workload(n, steps=K, kind=1, chi_mean=cm, chi_std=cs_, lc_cells=clc, seed=5,
+                   dt_ts=args.dt_ts)
+    w.omega = 2.0 * math.pi / (1.0e8 * w.ts)
+    v0, s0, c0, t0 = w.initial_state()
+    t_setup = time.time() - t_setup
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    st = {}
+    for name in ("mixed", "fp64"):
+        v, sg, c = (torch.from_numpy(a).to(dev) for a in (v0, s0, c0))
+        st[name] = (v, sg, c, make_state(v, sg, c, t0))
+    del v0, s0, c0
+    ctx = {name: Context(w.nx, w.ny, w.nz, w.h, I.TABLE1["K"], w.mu, bc=w.bc_values(),
+                         stz=w.stz, precision=prec, max_cycles=100, stream=stream)
+           for name, prec in (("mixed", MG_MIXED), ("fp64", MG_FP64))}
+    def max_sbar(sig):
+        # largest shear stress sqrt(s0:s0 / 2) over the cells
+        tr = (sig[0] + sig[1] + sig[2]) / 3.0
+        q = sum((sig[a] - tr) ** 2 for a in range(3)) + 2.0 * sum(sig[a] ** 2 for a in (3, 4, 5))
+        return float(torch.sqrt(0.5 * q.max()))
+
+    clocks = Clocks(0)
+    clocks.start()
+    rows, failed = [], None
+    for k in range(K):
+        row = {"step": k + 1}
+        for name in ("mixed", "fp64"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            status, stats = ctx[name].step(st[name][3], w.dt, TOL, raise_on_error=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name + "_ms"] = e0.elapsed_time(e1)
+            row[name + "_cycles"] = stats.cycles
+            row[name + "_rel_resid"] = stats.rel_resid
+            row[name + "_status"] = status
+            row[name + "_max_sbar"] = max_sbar(st[name][1])
+        for i, key in ((0, "v"), (1, "sigma")):
+            a, b = st["mixed"][i], st["fp64"][i]
+            row["err_" + key] = float(torch.linalg.vector_norm(a - b) /
+                                      torch.linalg.vector_norm(b))
+        rows.append(row)
+        if row["mixed_status"] or row["fp64_status"]:
+            failed = k + 1
+            break
+    clk = clocks.stop()
+    for c in ctx.values():
+        c.close()
+    ok_rows = [r for r in rows if not (r["mixed_status"] or r["fp64_status"])] or rows
+    tail = ok_rows[1:] if len(ok_rows) > 1 else ok_rows
+    mix = statistics.mean(r["mixed_ms"] for r in tail)
+    f64 = statistics.mean(r["fp64_ms"] for r in tail)
+    return {"mode": "disc", "grid": [n, n, n], "steps": K, "dt_ts": args.dt_ts,
+            "omega_rad_s": w.omega, "R_over_L": w.R,
+            "chi0": "%g K / %g K / l_c = %g cells, seed 5" % (cm, cs_, clc),
+            "mixed_ms_per_step": mix, "fp64_ms_per_step": f64, "speedup_mixed": f64 / mix,
+            "first_step_ms": {"mixed": rows[0]["mixed_ms"], "fp64": rows[0]["fp64_ms"]},
+            "max_err_v": max(r["err_v"] for r in ok_rows),
+            "max_err_sigma": max(r["err_sigma"] for r in ok_rows),
+            "worst_rel_resid": max(max(r["mixed_rel_resid"], r["fp64_rel_resid"]) for r in ok_rows),
+            "max_sbar_pa": max(r["fp64_max_sbar"] for r in rows), "failed_at_step": failed,
+            "host_setup_s": t_setup, "clocks": clk, "per_step": rows}
 
 
 def run_sweeps(args):
@@ -61,7 +148,8 @@ def run_sweeps(args):
 
     from paper_1904_03808_gb300 import MG_MIXED, Context
     from paper_1904_03808_gb300 import inputs as I
-    n, nz = args.n, args.nz or args.n
+    n = args.n or 256
+    nz = args.nz or n
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     ctx = Context(n, n, nz, 2.0e-2 / n, I.TABLE1["K"], I.TABLE1["mu"], precision=MG_MIXED,
@@ -227,7 +315,7 @@ def run_ours(args):
     Q.lib()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    w = workload(args.n)
+    w = workload(args.n or 256)
     v0, s0, c0, t0 = w.initial_state()
     K = args.steps
     W = max(args.warmup, 3)
@@ -396,7 +484,7 @@ def run_reference(args):
         return None
     import oracle as O
     O.build()
-    w = workload(args.n)
+    w = workload(args.n or 256)
     v, sig, chi, t = w.initial_state()
     # V-cycles per solve for this workload: one full oracle step at 64^3 of the
     # same recipe (multigrid cycle counts do not grow with the grid)
@@ -430,6 +518,8 @@ def main():
     args = parse()
     if args.sweep_only:
         out = run_sweeps(args)
+    elif args.disc:
+        out = run_disc(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

@@ -292,7 +292,9 @@ cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, cons
 // Measured on GB300 and dropped: one CTA per SM with double-buffered stages
 // and four z-plane slots (24% slower); issuing the next tile's right-hand
 // side and z-plane copies right after the first pass, when they are dead
-// (6% slower); a cyclic plane-major tile order (27%
+// (6% slower); right-hand-side rows loaded from global memory into
+// registers instead of staged (freeing shared memory for taller tiles or a
+// third CTA per SM: 10-17% slower); a cyclic plane-major tile order (27%
 // fewer DRAM bytes, 18% slower: it loses the z-plane reuse); one thread per
 // node component instead of per column pair (35% slower); natural instead of
 // parity-split column order (8% slower).
@@ -414,6 +416,7 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
 #define SZ(row, c, x) (Hs[AT(row, c, x)] + Ls[AT(row, c, x)])
         // right-hand side with the z-neighbour terms folded in
         float r[3][2][R];
+#define BV(c, e, x) Bs[AT(jj - 1, c, x)]
 #pragma unroll
         for (int jj = 1; jj < R - 1; jj++) {
             const float dOm0 = DZ(jj, 0, xom), dOm2 = DZ(jj, 2, xom);
@@ -421,20 +424,21 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
             const float dE0 = DZ(jj, 0, xe), dE2 = DZ(jj, 2, xe);
             const float dO0 = DZ(jj, 0, xo), dO2 = DZ(jj, 2, xo);
             // E node: x-1 is the neighbour's O column, x+1 the own O column
-            r[0][0][jj] = Bs[AT(jj - 1, 0, xe)] + (SZ(jj, 0, xe) + kq * (dO2 - dOm2));
-            r[1][0][jj] = Bs[AT(jj - 1, 1, xe)] +
+            r[0][0][jj] = BV(0, 0, xe) + (SZ(jj, 0, xe) + kq * (dO2 - dOm2));
+            r[1][0][jj] = BV(1, 0, xe) +
                           (SZ(jj, 1, xe) + kq * (DZ(jj + 1, 2, xe) - DZ(jj - 1, 2, xe)));
-            r[2][0][jj] = Bs[AT(jj - 1, 2, xe)] +
+            r[2][0][jj] = BV(2, 0, xe) +
                           (lp * SZ(jj, 2, xe) +
                            kq * ((dO0 - dOm0) + (DZ(jj + 1, 1, xe) - DZ(jj - 1, 1, xe))));
             // O node: x-1 is the own E column, x+1 the neighbour's E column
-            r[0][1][jj] = Bs[AT(jj - 1, 0, xo)] + (SZ(jj, 0, xo) + kq * (dEp2 - dE2));
-            r[1][1][jj] = Bs[AT(jj - 1, 1, xo)] +
+            r[0][1][jj] = BV(0, 1, xo) + (SZ(jj, 0, xo) + kq * (dEp2 - dE2));
+            r[1][1][jj] = BV(1, 1, xo) +
                           (SZ(jj, 1, xo) + kq * (DZ(jj + 1, 2, xo) - DZ(jj - 1, 2, xo)));
-            r[2][1][jj] = Bs[AT(jj - 1, 2, xo)] +
+            r[2][1][jj] = BV(2, 1, xo) +
                           (lp * SZ(jj, 2, xo) +
                            kq * ((dEp0 - dE0) + (DZ(jj + 1, 1, xo) - DZ(jj - 1, 1, xo))));
         }
+#undef BV
 #undef DZ
 #undef SZ
         float P[3][2][R];
