@@ -204,6 +204,13 @@ mg_status mg_level_stencil(const mg_ctx *ctx, int level, double *host_S);
  * level-sized corner arrays (3, nz_l+1, ny_l, nx_l); r must not alias x. */
 mg_status mg_residual(mg_ctx *ctx, int level, const double *b, const double *x, double *r);
 
+/* The same residual in FP32, as the mixed-precision inner V-cycles compute
+ * it (section 3.6 operator, single-precision arithmetic): float arrays in
+ * natural column order, r must not alias x.  On the finest level the arrays
+ * pass through the solver's own FP32 buffers, so this call must not overlap
+ * an mg_solve / qs_step on the same context. */
+mg_status mg_residual32(mg_ctx *ctx, int level, const float *b, const float *x, float *r);
+
 /* nsweeps Gauss-Seidel sweeps on level `level`, colours 0..7 if
  * descending == 0 else 7..0; FP64 (precision 0) or FP32 arrays (precision 1). */
 mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps, int descending,

@@ -78,6 +78,7 @@ _SIGS = {
     "mg_level_dims": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "mg_level_stencil": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
     "mg_residual": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "mg_residual32": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_smooth": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_int, C.c_int]),
     "mg_restrict": (C.c_int, [_P, C.c_int, _P, _P]),
     "mg_prolong_add": (C.c_int, [_P, C.c_int, _P, _P]),
@@ -225,6 +226,11 @@ class Context:
         import torch
         _check(lib().mg_residual(self.h, level, _ptr(b, torch.float64), _ptr(x, torch.float64),
                                  _ptr(r, torch.float64)), "mg_residual")
+
+    def residual32(self, level, b, x, r):
+        import torch
+        _check(lib().mg_residual32(self.h, level, _ptr(b, torch.float32), _ptr(x, torch.float32),
+                                   _ptr(r, torch.float32)), "mg_residual32")
 
     def smooth(self, level, b, x, nsweeps, descending=False):
         import torch

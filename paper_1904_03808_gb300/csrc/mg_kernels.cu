@@ -470,7 +470,19 @@ cudaError_t residual_fine(const Dims &d, const Fine<double> &f, const double *b,
 }
 cudaError_t residual_fine(const Dims &d, const Fine<float> &f, const float *b, const float *x,
                           float *r, cudaStream_t s, int split) {
-    return res_fine_t(d, f, b, x, r, s, split);
+    // whole-row strips where the rows fit (smoother_rows.cu), else one
+    // thread per node
+    cudaError_t e = residual_fine_rows(d, f, b, x, r, s, split);
+    if (e == cudaErrorNotSupported) return res_fine_t(d, f, b, x, r, s, split);
+    if (e != cudaSuccess) return e;
+    const long plane = (long)d.ny * d.nx;  // wall planes of r are zero
+    for (int a = 0; a < 3; a++) {
+        e = cudaMemsetAsync(r + a * d.cs, 0, plane * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(r + a * d.cs + (long)d.nz * plane, 0, plane * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 cudaError_t residual_coarse(const Dims &d, const Coarse<double> &c, const double *b,
                             const double *x, double *r, cudaStream_t s) {

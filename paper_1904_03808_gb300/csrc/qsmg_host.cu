@@ -1010,6 +1010,33 @@ mg_status mg_residual(mg_ctx *ctx, int level, const double *b, const double *x, 
     return MG_OK;
 }
 
+mg_status mg_residual32(mg_ctx *ctx, int level, const float *b, const float *x, float *r) {
+    CKS(level_arg(ctx, level, 0));
+    if (!b || !x || !r || r == x) {
+        set_err("mg_residual32: bad arrays");
+        return MG_ERR_ARG;
+    }
+    if (level == 0 && ctx->split0) {
+        // the caller's arrays are in natural order: through the solver's
+        // own parity-split finest FP32 buffers
+        const Dims &d = ctx->L[0];
+        const size_t plane = (size_t)d.ny * d.nx;
+        CK(split_columns(d, x, ctx->x32[0], true, ctx->st));
+        CK(split_columns(d, b, ctx->b32[0], true, ctx->st));
+        CKS(residual_level<float>(ctx, 0, ctx->b32[0], ctx->x32[0], ctx->r32[0]));
+        CK(split_columns(d, ctx->r32[0], r, false, ctx->st));
+        for (int c = 0; c < 3; c++) {  // the solver relies on zero walls in x32[0]
+            CK(cudaMemsetAsync(ctx->x32[0] + c * d.cs, 0, plane * sizeof(float), ctx->st));
+            CK(cudaMemsetAsync(ctx->x32[0] + c * d.cs + d.nz * plane, 0, plane * sizeof(float),
+                               ctx->st));
+        }
+    } else {
+        CKS(residual_level<float>(ctx, level, b, x, r));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
 mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps, int descending,
                     int precision) {
     CKS(level_arg(ctx, level, 0));

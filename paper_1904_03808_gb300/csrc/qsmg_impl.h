@@ -66,6 +66,10 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float 
 
 // one-time kernel attribute set-up of the sweeps (call before any capture)
 cudaError_t smoother_init();
+// FP32 finest-level residual with the persistent row-strip kernel;
+// cudaErrorNotSupported when the grid or the arrays do not suit it
+cudaError_t residual_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
+                               const float *x, float *r, cudaStream_t s, int split);
 // FP32 finest-level sweep vin -> vout with the row-strip kernels;
 // cudaErrorNotSupported when the rows are too long for them
 cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float *b,

@@ -52,13 +52,15 @@ __device__ __forceinline__ int wrap_mod(int a, int n) {
 // with D = H - L, streamed row by row so each plane value is loaded once.
 constexpr int kRowsMaxThreads = 256;  // rows up to 512 nodes
 
-// update the node of x-parity E at window row jj from the own column values
-// P, the far-side neighbour column X[c * sc + row * sr + xn] (shared memory)
-// and the folded right-hand side r
+// numerators of the node of x-parity E at window row jj: the folded
+// right-hand side r plus the in-plane neighbour terms, from the own column
+// values P and the far-side neighbour column X[c * sc + row * sr + xn]
+// (shared memory); the Gauss-Seidel update is numerator / d0, the residual
+// numerator - d0 x
 template <int E, int R>
-__device__ __forceinline__ void rows_update(float (&P)[3][2][R], float r0, float r1, float r2,
-                                            const float *X, int sc, int sr, int xn, int jj,
-                                            const Fine<float> &f) {
+__device__ __forceinline__ void rows_numer(const float (&P)[3][2][R], float r0, float r1,
+                                           float r2, const float *X, int sc, int sr, int xn,
+                                           int jj, const Fine<float> &f, float num[3]) {
     float m[3][3], p[3][3];  // [component][row jj-1, jj, jj+1] at x-1 and x+1
 #pragma unroll
     for (int q = 0; q < 3; q++)
@@ -75,19 +77,23 @@ __device__ __forceinline__ void rows_update(float (&P)[3][2][R], float r0, float
                 p[c][q] = nb;
             }
         }
-    const float lp = f.lp, kq = f.kq, dinv = f.dinv;
-    const float v0 = (r0 + lp * (m[0][1] + p[0][1]) +
-                      (P[0][E][jj - 1] + P[0][E][jj + 1]) +
-                      kq * (p[1][2] - p[1][0] - m[1][2] + m[1][0])) *
-                     dinv;
-    const float v1 = (r1 + lp * (P[1][E][jj - 1] + P[1][E][jj + 1]) +
-                      (m[1][1] + p[1][1]) + kq * (p[0][2] - p[0][0] - m[0][2] + m[0][0])) *
-                     dinv;
-    const float v2 =
-        (r2 + (m[2][1] + p[2][1]) + (P[2][E][jj - 1] + P[2][E][jj + 1])) * dinv;
-    P[0][E][jj] = v0;
-    P[1][E][jj] = v1;
-    P[2][E][jj] = v2;
+    const float lp = f.lp, kq = f.kq;
+    num[0] = r0 + lp * (m[0][1] + p[0][1]) + (P[0][E][jj - 1] + P[0][E][jj + 1]) +
+             kq * (p[1][2] - p[1][0] - m[1][2] + m[1][0]);
+    num[1] = r1 + lp * (P[1][E][jj - 1] + P[1][E][jj + 1]) + (m[1][1] + p[1][1]) +
+             kq * (p[0][2] - p[0][0] - m[0][2] + m[0][0]);
+    num[2] = r2 + (m[2][1] + p[2][1]) + (P[2][E][jj - 1] + P[2][E][jj + 1]);
+}
+
+// Gauss-Seidel update of the node of x-parity E at window row jj
+template <int E, int R>
+__device__ __forceinline__ void rows_update(float (&P)[3][2][R], float r0, float r1, float r2,
+                                            const float *X, int sc, int sr, int xn, int jj,
+                                            const Fine<float> &f) {
+    float num[3];
+    rows_numer<E, R>(P, r0, r1, r2, X, sc, sr, xn, jj, f, num);
+#pragma unroll
+    for (int c = 0; c < 3; c++) P[c][E][jj] = num[c] * f.dinv;
 }
 
 template <int TY, int F, bool SPLIT>
@@ -319,11 +325,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <int F, bool SPLIT>
+// RES: instead of a sweep phase, the residual b - A x of every plane
+// k = kbase, kbase + kstep, ... (F = 0, vin = zsrc = x, vout = r)
+template <int F, bool SPLIT, bool RES>
 __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
     k_gs_rows_p(Dims d, Fine<float> f, const float *__restrict__ b, const float *__restrict__ vin,
-                const float *__restrict__ zsrc, float *__restrict__ vout, int kbase, int nplanes,
-                int nstrips) {
+                const float *__restrict__ zsrc, float *__restrict__ vout, int kbase, int kstep,
+                int nplanes, int nstrips) {
     constexpr int TY = kPersTY, R = kPersR;
     extern __shared__ __align__(16) float sm[];
     const int nx = d.nx, ny = d.ny, hn = nx >> 1, cpr = nx >> 2;
@@ -359,7 +367,7 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
         const int pb = nplanes - blk * kPersPB < kPersPB ? nplanes - blk * kPersPB : kPersPB;
         const int rem = (int)(n - (long)blk * nstrips * kPersPB);
         s = rem / pb;
-        k = 2 * (blk * kPersPB + rem - s * pb) + kbase;
+        k = kstep * (blk * kPersPB + rem - s * pb) + kbase;
     };
     // z-plane slots 0, 1 (tag: strip * (nz + 1) + plane; uniform over the CTA)
     int tag0 = -1, tag1 = -1;
@@ -449,41 +457,65 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
                 P[c][0][jj] = Ps[AT(jj, c, xe)];
                 P[c][1][jj] = Ps[AT(jj, c, xo)];
             }
-        constexpr int EF = F, EG = 1 - F;
-        const int xF = EF == 0 ? xe : xo, xG = EG == 0 ? xe : xo;
-        const int nF = EF == 0 ? xom : xep, nG = EG == 0 ? xom : xep;
-        // pass 1: x-parity F on the odd rows
+        if (RES) {
+            // residual of the tile rows 1 .. TY: numerator - d0 x
+            float res[3][2][TY + 1];
 #pragma unroll
-        for (int jj = 1; jj < R - 1; jj += 2) {
-            rows_update<EF, R>(P, r[0][EF][jj], r[1][EF][jj], r[2][EF][jj], Ps, nx, 3 * nx, nF,
-                               jj, f);
+            for (int jj = 1; jj < TY + 1; jj++) {
+                float num[3];
+                rows_numer<0, R>(P, r[0][0][jj], r[1][0][jj], r[2][0][jj], Ps, nx, 3 * nx, xom,
+                                 jj, f, num);
 #pragma unroll
-            for (int c = 0; c < 3; c++) Ps[AT(jj, c, xF)] = P[c][EF][jj];
+                for (int c = 0; c < 3; c++) res[c][0][jj] = num[c] - f.d0 * P[c][0][jj];
+                rows_numer<1, R>(P, r[0][1][jj], r[1][1][jj], r[2][1][jj], Ps, nx, 3 * nx, xep,
+                                 jj, f, num);
+#pragma unroll
+                for (int c = 0; c < 3; c++) res[c][1][jj] = num[c] - f.d0 * P[c][1][jj];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+#pragma unroll
+                for (int jj = 1; jj < TY + 1; jj++) {
+                    P[c][0][jj] = res[c][0][jj];
+                    P[c][1][jj] = res[c][1][jj];
+                }
+        } else {
+            constexpr int EF = F, EG = 1 - F;
+            const int xF = EF == 0 ? xe : xo, xG = EG == 0 ? xe : xo;
+            const int nF = EF == 0 ? xom : xep, nG = EG == 0 ? xom : xep;
+            // pass 1: x-parity F on the odd rows
+    #pragma unroll
+            for (int jj = 1; jj < R - 1; jj += 2) {
+                rows_update<EF, R>(P, r[0][EF][jj], r[1][EF][jj], r[2][EF][jj], Ps, nx, 3 * nx, nF,
+                                   jj, f);
+    #pragma unroll
+                for (int c = 0; c < 3; c++) Ps[AT(jj, c, xF)] = P[c][EF][jj];
+            }
+            __syncthreads();
+            // pass 2: x-parity 1-F on the odd rows
+    #pragma unroll
+            for (int jj = 1; jj < R - 1; jj += 2) {
+                rows_update<EG, R>(P, r[0][EG][jj], r[1][EG][jj], r[2][EG][jj], Ps, nx, 3 * nx, nG,
+                                   jj, f);
+    #pragma unroll
+                for (int c = 0; c < 3; c++) Ps[AT(jj, c, xG)] = P[c][EG][jj];
+            }
+            __syncthreads();
+            // pass 3: x-parity F on the even rows
+    #pragma unroll
+            for (int jj = 2; jj < R - 2; jj += 2) {
+                rows_update<EF, R>(P, r[0][EF][jj], r[1][EF][jj], r[2][EF][jj], Ps, nx, 3 * nx, nF,
+                                   jj, f);
+    #pragma unroll
+                for (int c = 0; c < 3; c++) Ps[AT(jj, c, xF)] = P[c][EF][jj];
+            }
+            __syncthreads();
+            // pass 4: x-parity 1-F on the even rows
+    #pragma unroll
+            for (int jj = 2; jj < R - 2; jj += 2)
+                rows_update<EG, R>(P, r[0][EG][jj], r[1][EG][jj], r[2][EG][jj], Ps, nx, 3 * nx, nG,
+                                   jj, f);
         }
-        __syncthreads();
-        // pass 2: x-parity 1-F on the odd rows
-#pragma unroll
-        for (int jj = 1; jj < R - 1; jj += 2) {
-            rows_update<EG, R>(P, r[0][EG][jj], r[1][EG][jj], r[2][EG][jj], Ps, nx, 3 * nx, nG,
-                               jj, f);
-#pragma unroll
-            for (int c = 0; c < 3; c++) Ps[AT(jj, c, xG)] = P[c][EG][jj];
-        }
-        __syncthreads();
-        // pass 3: x-parity F on the even rows
-#pragma unroll
-        for (int jj = 2; jj < R - 2; jj += 2) {
-            rows_update<EF, R>(P, r[0][EF][jj], r[1][EF][jj], r[2][EF][jj], Ps, nx, 3 * nx, nF,
-                               jj, f);
-#pragma unroll
-            for (int c = 0; c < 3; c++) Ps[AT(jj, c, xF)] = P[c][EF][jj];
-        }
-        __syncthreads();
-        // pass 4: x-parity 1-F on the even rows
-#pragma unroll
-        for (int jj = 2; jj < R - 2; jj += 2)
-            rows_update<EG, R>(P, r[0][EG][jj], r[1][EG][jj], r[2][EG][jj], Ps, nx, 3 * nx, nG,
-                               jj, f);
 #undef AT
         // store the tile rows
         float *Ok = vout + (long)k * ps;
@@ -509,28 +541,42 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
 
 int g_sms[64];  // SM count per device, set by smoother_init
 
-template <int F, bool SPLIT>
+template <int F, bool SPLIT, bool RES>
 cudaError_t launch_rows_p(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
-                          const float *zsrc, float *vout, int par, cudaStream_t s, int sms) {
-    const int kbase = par ? 1 : 2;
-    const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
+                          const float *zsrc, float *vout, int kbase, int kstep, int nplanes,
+                          cudaStream_t s, int sms) {
     if (nplanes <= 0) return cudaSuccess;
     const int nstrips = (d.ny + kPersTY - 1) / kPersTY;
     const long ntiles = (long)nstrips * nplanes;
     const long slots = (long)sms * kPersMinBlocks;
     const int grid = (int)(ntiles < slots ? ntiles : slots);
-    k_gs_rows_p<F, SPLIT><<<grid, d.nx / 2, pers_floats(d.nx) * sizeof(float), s>>>(
-        d, f, b, vin, zsrc, vout, kbase, nplanes, nstrips);
+    k_gs_rows_p<F, SPLIT, RES><<<grid, d.nx / 2, pers_floats(d.nx) * sizeof(float), s>>>(
+        d, f, b, vin, zsrc, vout, kbase, kstep, nplanes, nstrips);
     count_launch();
     return cudaGetLastError();
 }
 
+// sweep phase over the planes of parity par (1: odd planes 1 .. nz-1, 0:
+// even planes 2 .. nz-2)
 template <int F>
 cudaError_t rows_p_phase(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
                          const float *zsrc, float *vout, int par, cudaStream_t s, int split,
                          int sms) {
-    return split ? launch_rows_p<F, true>(d, f, b, vin, zsrc, vout, par, s, sms)
-                 : launch_rows_p<F, false>(d, f, b, vin, zsrc, vout, par, s, sms);
+    const int kbase = par ? 1 : 2;
+    const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
+    return split ? launch_rows_p<F, true, false>(d, f, b, vin, zsrc, vout, kbase, 2, nplanes, s,
+                                                 sms)
+                 : launch_rows_p<F, false, false>(d, f, b, vin, zsrc, vout, kbase, 2, nplanes, s,
+                                                  sms);
+}
+
+// whether the persistent kernel takes this grid and these arrays; sms set
+bool rows_p_ok(const Dims &d, const void *a, const void *b, const void *c, int &sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    sms = (dev >= 0 && dev < 64) ? g_sms[dev] : 0;
+    const bool aligned = (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15) == 0;
+    return sms > 0 && aligned && d.nx % 64 == 0 && d.nx <= kPersMaxNx && d.ny >= kPersR;
 }
 
 }  // namespace
@@ -553,10 +599,12 @@ cudaError_t smoother_init() {
     SET((k_gs_rows<kRowsTY, 0, true>), smem)
     SET((k_gs_rows<kRowsTY, 1, false>), smem)
     SET((k_gs_rows<kRowsTY, 1, true>), smem)
-    SET((k_gs_rows_p<0, false>), smem_p)
-    SET((k_gs_rows_p<0, true>), smem_p)
-    SET((k_gs_rows_p<1, false>), smem_p)
-    SET((k_gs_rows_p<1, true>), smem_p)
+    SET((k_gs_rows_p<0, false, false>), smem_p)
+    SET((k_gs_rows_p<0, true, false>), smem_p)
+    SET((k_gs_rows_p<1, false, false>), smem_p)
+    SET((k_gs_rows_p<1, true, false>), smem_p)
+    SET((k_gs_rows_p<0, false, true>), smem_p)
+    SET((k_gs_rows_p<0, true, true>), smem_p)
 #undef SET
     return cudaSuccess;
 }
@@ -566,13 +614,9 @@ cudaError_t smoother_init() {
 cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
                                const float *vin, float *vout, bool descending, cudaStream_t s,
                                int split) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const int sms = (dev >= 0 && dev < 64) ? g_sms[dev] : 0;
-    const bool aligned =
-        (((uintptr_t)b | (uintptr_t)vin | (uintptr_t)vout) & 15) == 0;
-    if (sms > 0 && aligned && d.nx % 64 == 0 && d.nx <= kPersMaxNx && d.ny >= kPersR) {
+    int sms = 0;
+    cudaError_t e;
+    if (rows_p_ok(d, b, vin, vout, sms)) {
         if (!descending) {
             e = rows_p_phase<0>(d, f, b, vin, vin, vout, 0, s, split, sms);
             if (e != cudaSuccess) return e;
@@ -591,6 +635,16 @@ cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float 
     e = rows_phase<1>(d, f, b, vin, vin, vout, 1, s, split);
     if (e != cudaSuccess) return e;
     return rows_phase<1>(d, f, b, vin, vout, vout, 0, s, split);
+}
+
+// FP32 finest-level residual r = b - A x (interior planes) with the
+// persistent row-strip kernel, or cudaErrorNotSupported
+cudaError_t residual_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
+                               const float *x, float *r, cudaStream_t s, int split) {
+    int sms = 0;
+    if (!rows_p_ok(d, b, x, r, sms)) return cudaErrorNotSupported;
+    return split ? launch_rows_p<0, true, true>(d, f, b, x, x, r, 1, 1, d.nz - 1, s, sms)
+                 : launch_rows_p<0, false, true>(d, f, b, x, x, r, 1, 1, d.nz - 1, s, sms);
 }
 
 }  // namespace qsmg

@@ -65,6 +65,31 @@ def test_hierarchy_and_galerkin_tables(shape):
         assert np.allclose(S_gpu, S_ora, rtol=0, atol=1e-14 * np.abs(S_ora).max())
 
 
+@pytest.mark.parametrize("shape", [(64, 32, 32), (256, 32, 32), (128, 40, 32), (72, 40, 16),
+                                   (16, 8, 12)])
+def test_residual32_every_level(shape):
+    """FP32 residual of the mixed-precision V-cycles against the oracle's on
+    the same (FP32-rounded) arrays: the persistent row-strip kernel on the
+    finest level for rows of 64/128/256 nodes with at least 9 rows (ragged
+    strips at ny = 40), one thread per node otherwise, coarse levels."""
+    rng = np.random.default_rng(11)
+    ctx = ctx_for(shape, precision=MG_MIXED)
+    mg = O.MG(*shape, LAM, MU)
+    for l in range(max(mg.levels - 1, 1)):
+        d = mg.dims(l)
+        x = rand_corner(rng, d).astype(np.float32).astype(np.float64)
+        b = rand_corner(rng, d).astype(np.float32).astype(np.float64)
+        if l > 0:
+            x[:, [0, d[2]]] = 0
+        r = torch.full(x.shape, float("nan"), device="cuda", dtype=torch.float32)
+        ctx.residual32(l, g(b, torch.float32), g(x, torch.float32), r)
+        want = O.residual(mg.stencil(l), b, x)
+        got = c(r).astype(np.float64)
+        assert np.isfinite(got).all()
+        assert rel(got, want) <= 1e-6, (l, rel(got, want))
+    ctx.close()
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_residual_every_level(shape):
     rng = np.random.default_rng(1)
