@@ -307,27 +307,60 @@ __global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restric
 }
 
 // prolongation x += T xc: fine node 2I is coarse node I, odd fine nodes take
-// the mean of their two neighbours along each odd axis (coarse walls are 0)
+// the mean of their two neighbours along each odd axis (coarse walls are 0).
+// One thread per coarse cell (I, J, K): it loads the cell's 8 corners once
+// per component, interpolates separably (x, then y, then z) and adds into
+// its 2 x 2 x 2 block of fine nodes (2I+a, 2J+b, 2K+c), wall plane 0 skipped.
 template <typename T>
 __global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restrict__ x, int split) {
-    int i, j, k;
-    if (!node_ijk(f, i, j, k)) return;
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int I1 = (i & 1) ? ((I0 + 1 < c.nx) ? I0 + 1 : 0) : I0;
-    const int J1 = (j & 1) ? ((J0 + 1 < c.ny) ? J0 + 1 : 0) : J0;
-    const int K1 = (k & 1) ? K0 + 1 : K0;
-    const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1), wz = (k & 1) ? T(0.5) : T(1);
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-    const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
-    const long p = ((long)k * f.ny + j) * f.nx + colmap(i, f.nx, split);
+    const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I >= c.nx || J >= c.ny) return;
+    const int I1 = I + 1 < c.nx ? I + 1 : 0, J1 = J + 1 < c.ny ? J + 1 : 0;
+    const long cps = (long)c.nx * c.ny, fps = (long)f.nx * f.ny;
+    const long cr[2] = {(long)J * c.nx, (long)J1 * c.nx};
+    const int ci[2] = {I, I1};
+    const int fcol[2] = {colmap(2 * I, f.nx, split), colmap(2 * I + 1, f.nx, split)};
+    const T h = T(0.5);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        T s = 0;
-        for (int u = 0; u < nk; u++)
-            for (int v = 0; v < nj; v++)
-                for (int w = 0; w < ni; w++)
-                    s += xc[a * c.cs + ((long)Ks[u] * c.ny + Js[v]) * c.nx + Is[w]];
-        x[p + a * f.cs] += wx * wy * wz * s;
+        const T *X = xc + a * c.cs + (long)K * cps;
+        T v[2][2][2];  // [z][y][x] corners
+#pragma unroll
+        for (int z = 0; z < 2; z++)
+#pragma unroll
+            for (int y = 0; y < 2; y++)
+#pragma unroll
+                for (int e = 0; e < 2; e++) v[z][y][e] = X[z * cps + cr[y] + ci[e]];
+        T w[2][2][2];  // [fine c][fine b][fine a]
+#pragma unroll
+        for (int z = 0; z < 2; z++) {
+            T ax[2][2];  // [y][fine a]
+#pragma unroll
+            for (int y = 0; y < 2; y++) {
+                ax[y][0] = v[z][y][0];
+                ax[y][1] = h * (v[z][y][0] + v[z][y][1]);
+            }
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                w[z][0][e] = ax[0][e];
+                w[z][1][e] = h * (ax[0][e] + ax[1][e]);
+            }
+        }
+#pragma unroll
+        for (int cz = 0; cz < 2; cz++) {
+            const int k = 2 * K + cz;
+            if (k == 0) continue;
+#pragma unroll
+            for (int bb = 0; bb < 2; bb++) {
+                T *row = x + a * f.cs + (long)k * fps + (long)(2 * J + bb) * f.nx;
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const T val = cz ? h * (w[0][bb][e] + w[1][bb][e]) : w[0][bb][e];
+                    row[fcol[e]] += val;
+                }
+            }
+        }
     }
 }
 
@@ -536,7 +569,7 @@ cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_
 template <typename T>
 static cudaError_t prolong_t(const Dims &f, const T *xc, T *x, cudaStream_t s, int split) {
     const Dims c = make_dims(f.nx / 2, f.ny / 2, f.nz / 2);
-    k_prolong<T><<<node_grid(f.nx, f.ny, f.nz - 1), kBlock, 0, s>>>(f, c, xc, x, split);
+    k_prolong<T><<<node_grid(c.nx, c.ny, c.nz), kBlock, 0, s>>>(f, c, xc, x, split);
     count_launch();
     return cudaGetLastError();
 }
