@@ -393,15 +393,15 @@ mg_status sweeps(mg_ctx *ctx, int l, const T *b, T *x, int n, bool descending) {
     return sweeps_colour<T>(ctx, l, b, x, n, descending);
 }
 
-// FP32: the tiled two-phase kernels, except on large coarse levels where the
-// 27-point tiled kernel (128 registers, 2 CTAs per SM) loses to colour
-// launches (measured on GB300 at 128^2 planes: 71 us per phase launch against
-// 4 x 13 us)
+// FP32: the two-phase kernels (row strips where the rows fit, else tiles),
+// except on large coarse levels without row strips, where the 27-point tile
+// kernel (128 registers, 2 CTAs per SM) loses to colour launches (measured on
+// GB300 at 128^2 planes: 71 us per phase launch against 4 x 13 us)
 template <>
 mg_status sweeps<float>(mg_ctx *ctx, int l, const float *b, float *x, int n, bool descending) {
     const Dims &d = ctx->L[l];
     const bool colour = (ctx->opts.flags & MG_FLAG_COLOUR_PASSES) ||
-                        (l > 0 && (long)d.nx * d.ny >= 128L * 128L);
+                        (l > 0 && (long)d.nx * d.ny >= 128L * 128L && !coarse_rows_fit(d));
     if (!colour) return sweeps_tiled(ctx, l, b, x, n, descending);
     return sweeps_colour<float>(ctx, l, b, x, n, descending);
 }

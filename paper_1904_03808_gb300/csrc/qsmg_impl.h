@@ -70,6 +70,12 @@ cudaError_t smoother_init();
 // cudaErrorNotSupported when the grid or the arrays do not suit it
 cudaError_t residual_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
                                const float *x, float *r, cudaStream_t s, int split);
+// coarse-level FP32 sweep with the persistent row-strip kernel (27-point
+// block stencil); cudaErrorNotSupported when it does not apply.
+// coarse_rows_fit: whether a level of these dimensions takes it.
+bool coarse_rows_fit(const Dims &d);
+cudaError_t gs_sweep_coarse_rows(const Dims &d, const Coarse<float> &c, const float *b,
+                                 const float *vin, float *vout, bool descending, cudaStream_t s);
 // FP32 finest-level sweep vin -> vout with the row-strip kernels;
 // cudaErrorNotSupported when the rows are too long for them
 cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float *b,

@@ -374,6 +374,9 @@ cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float
 
 cudaError_t gs_sweep_coarse_tiled(const Dims &d, const Coarse<float> &c, const float *b,
                                   const float *vin, float *vout, bool descending, cudaStream_t s) {
+    // whole-row strips where the rows fit (smoother_rows.cu)
+    const cudaError_t e = gs_sweep_coarse_rows(d, c, b, vin, vout, descending, s);
+    if (e != cudaErrorNotSupported) return e;
     CoarseOp<float> op{c};
     return sweep<float>(d, op, b, vin, vout, descending, s, 0);
 }

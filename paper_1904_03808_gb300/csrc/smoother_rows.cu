@@ -1,16 +1,20 @@
-// smoother_rows.cu -- row-strip Gauss-Seidel sweep phases for the finest
-// level (structured 19-point operator of the scaled Eq. 30, FP32).
+// smoother_rows.cu -- row-strip Gauss-Seidel sweep phases (FP32) for the
+// finest level (structured 19-point operator of the scaled Eq. 30) and for
+// coarse levels of rows >= 128 nodes (27-point block stencil, Eq. 36), and
+// the finest-level residual.
 //
 // One 8-colour sweep runs as two phase launches, as in smoother_fast.cu:
 // the planes of one k-parity (4 in-plane colours each, reading the old
 // z-neighbour planes), then the planes of the other parity (reading the
 // first phase's output).  Here a CTA owns whole rows of a plane, so the
 // periodic x direction needs no halo.  Two kernels:
-//   k_gs_rows_p  persistent (one CTA per SM) for rows of 64, 128 or 256
-//                nodes: the rows of the next tile are copied into shared
-//                memory with cp.async while the current tile computes;
+//   k_gs_rows_p  persistent, for rows of 64, 128 or 256 nodes: the rows of
+//                each tile are copied into shared memory with cp.async while
+//                the other CTAs on the SM compute; templated on the operator
+//                (FineRowsOp, CoarseRowsOp) and, with RES, computing the
+//                residual b - A x instead of a sweep phase;
 //   k_gs_rows    one CTA per tile, operands loaded straight into registers,
-//                for the other rows of up to 512 nodes.
+//                for the other finest rows of up to 512 nodes.
 // Both compute every node from the same neighbour values as the sequential
 // colour order (tested against the eight colour launches).
 #include <stdint.h>
@@ -280,7 +284,8 @@ cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, cons
 
 
 // ------------------------------------------------------------------------
-// Persistent kernel.  Two CTAs per SM (128 threads each at nx = 256), each
+// Persistent kernel.  Two CTAs per SM at nx = 256 (128 threads each; four at
+// 128, eight at 64), each
 // walking a contiguous run of the phase's tiles (strip, plane).  Tiles are
 // ordered by blocks of kPersPB planes, then strip, then plane: consecutive
 // tiles are mostly consecutive planes of one strip and share a z-neighbour
@@ -306,7 +311,7 @@ cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, cons
 // parity-split column order (8% slower).
 constexpr int kPersTY = 6;
 constexpr int kPersR = kPersTY + 3;
-constexpr int kPersMinBlocks = 2;  // resident CTAs per SM
+constexpr int kPersMinBlocks = 2;  // resident CTAs per SM at nx = 256 (more for shorter rows)
 constexpr int kPersMaxNx = 256;
 constexpr int kPersPB = 16;  // planes per block of the tile order
 
@@ -325,11 +330,181 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// RES: instead of a sweep phase, the residual b - A x of every plane
-// k = kbase, kbase + kstep, ... (F = 0, vin = zsrc = x, vout = r)
-template <int F, bool SPLIT, bool RES>
+// Shared rows of a tile: [row][component][nx]; the own column pair of a
+// thread is (xe, xo), the far-side neighbours xom (x - 1 of the E node) and
+// xep (x + 1 of the O node).
+struct RowCols {
+    int nx, xe, xo, xom, xep;
+    __device__ __forceinline__ int at(int row, int c, int x) const {
+        return (row * 3 + c) * nx + x;
+    }
+};
+
+// Finest level: the structured 19-point operator (scaled Eq. 30).
+struct FineRowsOp {
+    Fine<float> f;
+    // right-hand side of window rows 1 .. R-2 with the z-neighbour terms
+    // folded in (L, H: the lower and upper neighbour planes, B: b rows 1..R-2)
+    template <int R>
+    __device__ __forceinline__ void fold(float (&r)[3][2][R], const float *Ls, const float *Hs,
+                                         const float *Bs, const RowCols &q) const {
+        const float lp = f.lp, kq = f.kq;
+        const int xe = q.xe, xo = q.xo, xom = q.xom, xep = q.xep;
+#define DZ(row, c, x) (Hs[q.at(row, c, x)] - Ls[q.at(row, c, x)])
+#define SZ(row, c, x) (Hs[q.at(row, c, x)] + Ls[q.at(row, c, x)])
+#define BV(c, x) Bs[q.at(jj - 1, c, x)]
+#pragma unroll
+        for (int jj = 1; jj < R - 1; jj++) {
+            const float dOm0 = DZ(jj, 0, xom), dOm2 = DZ(jj, 2, xom);
+            const float dEp0 = DZ(jj, 0, xep), dEp2 = DZ(jj, 2, xep);
+            const float dE0 = DZ(jj, 0, xe), dE2 = DZ(jj, 2, xe);
+            const float dO0 = DZ(jj, 0, xo), dO2 = DZ(jj, 2, xo);
+            // E node: x-1 is the neighbour's O column, x+1 the own O column
+            r[0][0][jj] = BV(0, xe) + (SZ(jj, 0, xe) + kq * (dO2 - dOm2));
+            r[1][0][jj] =
+                BV(1, xe) + (SZ(jj, 1, xe) + kq * (DZ(jj + 1, 2, xe) - DZ(jj - 1, 2, xe)));
+            r[2][0][jj] = BV(2, xe) + (lp * SZ(jj, 2, xe) +
+                                       kq * ((dO0 - dOm0) + (DZ(jj + 1, 1, xe) - DZ(jj - 1, 1, xe))));
+            // O node: x-1 is the own E column, x+1 the neighbour's E column
+            r[0][1][jj] = BV(0, xo) + (SZ(jj, 0, xo) + kq * (dEp2 - dE2));
+            r[1][1][jj] =
+                BV(1, xo) + (SZ(jj, 1, xo) + kq * (DZ(jj + 1, 2, xo) - DZ(jj - 1, 2, xo)));
+            r[2][1][jj] = BV(2, xo) + (lp * SZ(jj, 2, xo) +
+                                       kq * ((dEp0 - dE0) + (DZ(jj + 1, 1, xo) - DZ(jj - 1, 1, xo))));
+        }
+#undef DZ
+#undef SZ
+#undef BV
+    }
+    template <int E, int R>
+    __device__ __forceinline__ void numer(const float (&P)[3][2][R], const float (&r)[3][2][R],
+                                          const float *X, const RowCols &q, int jj,
+                                          float num[3]) const {
+        rows_numer<E, R>(P, r[0][E][jj], r[1][E][jj], r[2][E][jj], X, q.nx, 3 * q.nx,
+                         E == 0 ? q.xom : q.xep, jj, f, num);
+    }
+    __device__ __forceinline__ void solve(const float num[3], float out[3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; a++) out[a] = num[a] * f.dinv;
+    }
+    __device__ __forceinline__ void centre(const float x[3], float out[3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; a++) out[a] = f.d0 * x[a];
+    }
+};
+
+// Coarse levels: one constant 27-point stencil of 3x3 blocks (Galerkin
+// product, Eq. 36), S[dd][a][b] with dd = 9 (dz+1) + 3 (dy+1) + (dx+1); the
+// walls are zero planes, so the stencil needs no truncation here.  Coarse
+// arrays are in natural column order, where a thread's E and O nodes are
+// adjacent: every shared row is read as 8-byte (E, O) pairs -- the own pair
+// and the pairs to the left (whose O is x - 1 of E) and right (whose E is
+// x + 1 of O).
+struct CoarseRowsOp {
+    Coarse<float> c;
+    __device__ __forceinline__ static float2 pair(const float *A, const RowCols &q, int row,
+                                                  int comp, int x2) {
+        return *reinterpret_cast<const float2 *>(&A[q.at(row, comp, x2)]);
+    }
+    template <int R>
+    __device__ __forceinline__ void fold(float (&r)[3][2][R], const float *Ls, const float *Hs,
+                                         const float *Bs, const RowCols &q) const {
+        const int xl = q.xom - 1, xr = q.xep;  // first columns of the left / right pairs
+#pragma unroll
+        for (int jj = 1; jj < R - 1; jj++) {
+            float sE[3] = {0.f, 0.f, 0.f}, sO[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int dz = -1; dz <= 1; dz += 2) {
+                const float *Z = dz < 0 ? Ls : Hs;
+#pragma unroll
+                for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        const float2 lft = pair(Z, q, jj + dy, d, xl);
+                        const float2 own = pair(Z, q, jj + dy, d, q.xe);
+                        const float2 rgt = pair(Z, q, jj + dy, d, xr);
+                        const float uE[3] = {lft.y, own.x, own.y}, uO[3] = {own.x, own.y, rgt.x};
+#pragma unroll
+                        for (int dx = 0; dx < 3; dx++) {
+                            const float *S = c.S + ((dz + 1) * 9 + (dy + 1) * 3 + dx) * 9 + d;
+#pragma unroll
+                            for (int a = 0; a < 3; a++) {
+                                sE[a] += S[3 * a] * uE[dx];
+                                sO[a] += S[3 * a] * uO[dx];
+                            }
+                        }
+                    }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float2 bb = pair(Bs, q, jj - 1, a, q.xe);
+                r[a][0][jj] = bb.x - sE[a];
+                r[a][1][jj] = bb.y - sO[a];
+            }
+        }
+    }
+    template <int E, int R>
+    __device__ __forceinline__ void numer(const float (&P)[3][2][R], const float (&r)[3][2][R],
+                                          const float *X, const RowCols &q, int jj,
+                                          float num[3]) const {
+        float s[3] = {0.f, 0.f, 0.f};
+        const int xfar = E == 0 ? q.xom - 1 : q.xep;  // the far-side neighbour's pair
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++) {
+            float far[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const float2 p2 = pair(X, q, jj + dy, d, xfar);
+                far[d] = E == 0 ? p2.y : p2.x;
+            }
+#pragma unroll
+            for (int dx = -1; dx <= 1; dx++) {
+                if (dy == 0 && dx == 0) continue;
+                // x - 1 of E / x + 1 of O: the far-side column; otherwise the
+                // own E (offset 0 of E, -1 of O) or the own O column
+                const bool isfar = E == 0 ? dx < 0 : dx > 0;
+                const int own = E == 0 ? (dx == 0 ? 0 : 1) : (dx == 0 ? 1 : 0);
+                const float *S = c.S + (9 + (dy + 1) * 3 + (dx + 1)) * 9;
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const float u = isfar ? far[d] : P[d][own][jj + dy];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) s[a] += S[3 * a + d] * u;
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) num[a] = r[a][E][jj] - s[a];
+    }
+    __device__ __forceinline__ void solve(const float num[3], float out[3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            out[a] = c.Dinv[3 * a] * num[0] + c.Dinv[3 * a + 1] * num[1] + c.Dinv[3 * a + 2] * num[2];
+    }
+    __device__ __forceinline__ void centre(const float x[3], float out[3]) const {
+        const float *S = c.S + 13 * 9;
+#pragma unroll
+        for (int a = 0; a < 3; a++) out[a] = S[3 * a] * x[0] + S[3 * a + 1] * x[1] + S[3 * a + 2] * x[2];
+    }
+};
+
+// Gauss-Seidel update of the node of x-parity E at window row jj
+template <int E, int R, class OP>
+__device__ __forceinline__ void pers_update(const OP &op, float (&P)[3][2][R],
+                                            const float (&r)[3][2][R], const float *X,
+                                            const RowCols &q, int jj) {
+    float num[3], out[3];
+    op.template numer<E, R>(P, r, X, q, jj, num);
+    op.solve(num, out);
+#pragma unroll
+    for (int c = 0; c < 3; c++) P[c][E][jj] = out[c];
+}
+
+// One sweep phase (or, with RES, the residual b - A x of every plane
+// k = kbase, kbase + kstep, ...; then F = 0, vin = zsrc = x, vout = r).
+template <class OP, int F, bool SPLIT, bool RES>
 __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
-    k_gs_rows_p(Dims d, Fine<float> f, const float *__restrict__ b, const float *__restrict__ vin,
+    k_gs_rows_p(Dims d, OP op, const float *__restrict__ b, const float *__restrict__ vin,
                 const float *__restrict__ zsrc, float *__restrict__ vout, int kbase, int kstep,
                 int nplanes, int nstrips) {
     constexpr int TY = kPersTY, R = kPersR;
@@ -341,16 +516,19 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
     const int t = threadIdx.x;
     const int q4 = 4 * (t % cpr), g = t / cpr;
     const int tm = t == 0 ? hn - 1 : t - 1, tp = t + 1 == hn ? 0 : t + 1;
-    const int xe = SPLIT ? t : 2 * t, xo = SPLIT ? hn + t : 2 * t + 1;
-    const int xom = SPLIT ? hn + tm : 2 * tm + 1;  // x - 1 of the E node
-    const int xep = SPLIT ? tp : 2 * tp;           // x + 1 of the O node
+    RowCols q;
+    q.nx = nx;
+    q.xe = SPLIT ? t : 2 * t;
+    q.xo = SPLIT ? hn + t : 2 * t + 1;
+    q.xom = SPLIT ? hn + tm : 2 * tm + 1;
+    q.xep = SPLIT ? tp : 2 * tp;
     const long ntiles = (long)nstrips * nplanes;
     const long n0 = blockIdx.x * ntiles / gridDim.x, n1 = (blockIdx.x + 1) * ntiles / gridDim.x;
     if (n0 >= n1) return;
 
-    // window rows [jlo, jhi) of plane q of src into dst (rows from jlo)
-    auto copy_rows = [&](float *dst, const float *src, int q, int y0, int jlo, int jhi) {
-        const float *base = src + (long)q * ps + q4;
+    // window rows [jlo, jhi) of plane qq of src into dst (rows from jlo)
+    auto copy_rows = [&](float *dst, const float *src, int qq, int y0, int jlo, int jhi) {
+        const float *base = src + (long)qq * ps + q4;
         for (int jj = jlo + g; jj < jhi; jj += 2) {
             int y = y0 - 1 - F + jj;  // ny >= R: at most one wrap
             y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
@@ -407,70 +585,50 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
         cp_async_commit();
     };
 
-    const float lp = f.lp, kq = f.kq;
     int sL, sH;
     issue_bz(n0, sL, sH);
     issue_p(n0);
     for (long n = n0; n < n1; n++) {
         cp_async_wait_all();
         __syncthreads();
-        const int cL = sL, cH = sH;
         int s, k;
         tile_of(n, s, k);
         const int y0 = s * TY;
-        const float *Ls = Zs0 + cL * plane_f, *Hs = Zs0 + cH * plane_f;
-#define AT(row, c, x) ((((row) * 3) + (c)) * nx + (x))
-#define DZ(row, c, x) (Hs[AT(row, c, x)] - Ls[AT(row, c, x)])
-#define SZ(row, c, x) (Hs[AT(row, c, x)] + Ls[AT(row, c, x)])
         // right-hand side with the z-neighbour terms folded in
         float r[3][2][R];
-#define BV(c, e, x) Bs[AT(jj - 1, c, x)]
-#pragma unroll
-        for (int jj = 1; jj < R - 1; jj++) {
-            const float dOm0 = DZ(jj, 0, xom), dOm2 = DZ(jj, 2, xom);
-            const float dEp0 = DZ(jj, 0, xep), dEp2 = DZ(jj, 2, xep);
-            const float dE0 = DZ(jj, 0, xe), dE2 = DZ(jj, 2, xe);
-            const float dO0 = DZ(jj, 0, xo), dO2 = DZ(jj, 2, xo);
-            // E node: x-1 is the neighbour's O column, x+1 the own O column
-            r[0][0][jj] = BV(0, 0, xe) + (SZ(jj, 0, xe) + kq * (dO2 - dOm2));
-            r[1][0][jj] = BV(1, 0, xe) +
-                          (SZ(jj, 1, xe) + kq * (DZ(jj + 1, 2, xe) - DZ(jj - 1, 2, xe)));
-            r[2][0][jj] = BV(2, 0, xe) +
-                          (lp * SZ(jj, 2, xe) +
-                           kq * ((dO0 - dOm0) + (DZ(jj + 1, 1, xe) - DZ(jj - 1, 1, xe))));
-            // O node: x-1 is the own E column, x+1 the neighbour's E column
-            r[0][1][jj] = BV(0, 1, xo) + (SZ(jj, 0, xo) + kq * (dEp2 - dE2));
-            r[1][1][jj] = BV(1, 1, xo) +
-                          (SZ(jj, 1, xo) + kq * (DZ(jj + 1, 2, xo) - DZ(jj - 1, 2, xo)));
-            r[2][1][jj] = BV(2, 1, xo) +
-                          (lp * SZ(jj, 2, xo) +
-                           kq * ((dEp0 - dE0) + (DZ(jj + 1, 1, xo) - DZ(jj - 1, 1, xo))));
-        }
-#undef BV
-#undef DZ
-#undef SZ
+        op.template fold<R>(r, Zs0 + sL * plane_f, Zs0 + sH * plane_f, Bs, q);
         float P[3][2][R];
 #pragma unroll
         for (int c = 0; c < 3; c++)
 #pragma unroll
             for (int jj = 0; jj < R; jj++) {
-                P[c][0][jj] = Ps[AT(jj, c, xe)];
-                P[c][1][jj] = Ps[AT(jj, c, xo)];
+                if (SPLIT) {
+                    P[c][0][jj] = Ps[q.at(jj, c, q.xe)];
+                    P[c][1][jj] = Ps[q.at(jj, c, q.xo)];
+                } else {  // adjacent: one 8-byte load
+                    const float2 v = *reinterpret_cast<const float2 *>(&Ps[q.at(jj, c, q.xe)]);
+                    P[c][0][jj] = v.x;
+                    P[c][1][jj] = v.y;
+                }
             }
         if (RES) {
-            // residual of the tile rows 1 .. TY: numerator - d0 x
+            // residual of the tile rows 1 .. TY: numerator - centre block x
             float res[3][2][TY + 1];
 #pragma unroll
             for (int jj = 1; jj < TY + 1; jj++) {
-                float num[3];
-                rows_numer<0, R>(P, r[0][0][jj], r[1][0][jj], r[2][0][jj], Ps, nx, 3 * nx, xom,
-                                 jj, f, num);
+                float num[3], x[3], cx[3];
+                op.template numer<0, R>(P, r, Ps, q, jj, num);
 #pragma unroll
-                for (int c = 0; c < 3; c++) res[c][0][jj] = num[c] - f.d0 * P[c][0][jj];
-                rows_numer<1, R>(P, r[0][1][jj], r[1][1][jj], r[2][1][jj], Ps, nx, 3 * nx, xep,
-                                 jj, f, num);
+                for (int c = 0; c < 3; c++) x[c] = P[c][0][jj];
+                op.centre(x, cx);
 #pragma unroll
-                for (int c = 0; c < 3; c++) res[c][1][jj] = num[c] - f.d0 * P[c][1][jj];
+                for (int c = 0; c < 3; c++) res[c][0][jj] = num[c] - cx[c];
+                op.template numer<1, R>(P, r, Ps, q, jj, num);
+#pragma unroll
+                for (int c = 0; c < 3; c++) x[c] = P[c][1][jj];
+                op.centre(x, cx);
+#pragma unroll
+                for (int c = 0; c < 3; c++) res[c][1][jj] = num[c] - cx[c];
             }
 #pragma unroll
             for (int c = 0; c < 3; c++)
@@ -481,42 +639,35 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
                 }
         } else {
             constexpr int EF = F, EG = 1 - F;
-            const int xF = EF == 0 ? xe : xo, xG = EG == 0 ? xe : xo;
-            const int nF = EF == 0 ? xom : xep, nG = EG == 0 ? xom : xep;
+            const int xF = EF == 0 ? q.xe : q.xo, xG = EG == 0 ? q.xe : q.xo;
             // pass 1: x-parity F on the odd rows
-    #pragma unroll
+#pragma unroll
             for (int jj = 1; jj < R - 1; jj += 2) {
-                rows_update<EF, R>(P, r[0][EF][jj], r[1][EF][jj], r[2][EF][jj], Ps, nx, 3 * nx, nF,
-                                   jj, f);
-    #pragma unroll
-                for (int c = 0; c < 3; c++) Ps[AT(jj, c, xF)] = P[c][EF][jj];
+                pers_update<EF, R>(op, P, r, Ps, q, jj);
+#pragma unroll
+                for (int c = 0; c < 3; c++) Ps[q.at(jj, c, xF)] = P[c][EF][jj];
             }
             __syncthreads();
             // pass 2: x-parity 1-F on the odd rows
-    #pragma unroll
+#pragma unroll
             for (int jj = 1; jj < R - 1; jj += 2) {
-                rows_update<EG, R>(P, r[0][EG][jj], r[1][EG][jj], r[2][EG][jj], Ps, nx, 3 * nx, nG,
-                                   jj, f);
-    #pragma unroll
-                for (int c = 0; c < 3; c++) Ps[AT(jj, c, xG)] = P[c][EG][jj];
+                pers_update<EG, R>(op, P, r, Ps, q, jj);
+#pragma unroll
+                for (int c = 0; c < 3; c++) Ps[q.at(jj, c, xG)] = P[c][EG][jj];
             }
             __syncthreads();
             // pass 3: x-parity F on the even rows
-    #pragma unroll
+#pragma unroll
             for (int jj = 2; jj < R - 2; jj += 2) {
-                rows_update<EF, R>(P, r[0][EF][jj], r[1][EF][jj], r[2][EF][jj], Ps, nx, 3 * nx, nF,
-                                   jj, f);
-    #pragma unroll
-                for (int c = 0; c < 3; c++) Ps[AT(jj, c, xF)] = P[c][EF][jj];
+                pers_update<EF, R>(op, P, r, Ps, q, jj);
+#pragma unroll
+                for (int c = 0; c < 3; c++) Ps[q.at(jj, c, xF)] = P[c][EF][jj];
             }
             __syncthreads();
             // pass 4: x-parity 1-F on the even rows
-    #pragma unroll
-            for (int jj = 2; jj < R - 2; jj += 2)
-                rows_update<EG, R>(P, r[0][EG][jj], r[1][EG][jj], r[2][EG][jj], Ps, nx, 3 * nx, nG,
-                                   jj, f);
+#pragma unroll
+            for (int jj = 2; jj < R - 2; jj += 2) pers_update<EG, R>(op, P, r, Ps, q, jj);
         }
-#undef AT
         // store the tile rows
         float *Ok = vout + (long)k * ps;
 #pragma unroll
@@ -525,8 +676,8 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
             if (y < ny) {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    Ok[c * cs + (long)y * nx + xe] = P[c][0][jj];
-                    Ok[c * cs + (long)y * nx + xo] = P[c][1][jj];
+                    Ok[c * cs + (long)y * nx + q.xe] = P[c][0][jj];
+                    Ok[c * cs + (long)y * nx + q.xo] = P[c][1][jj];
                 }
             }
         }
@@ -541,42 +692,56 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
 
 int g_sms[64];  // SM count per device, set by smoother_init
 
-template <int F, bool SPLIT, bool RES>
-cudaError_t launch_rows_p(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
+// resident CTAs of the persistent kernel per SM: shared memory and registers
+// scale with the row length (two CTAs at nx = 256, four at 128, eight at 64)
+inline long pers_slots(int nx, int sms) {
+    return (long)sms * kPersMinBlocks * (kPersMaxNx / nx);
+}
+
+template <class OP, int F, bool SPLIT, bool RES>
+cudaError_t launch_rows_p(const Dims &d, const OP &op, const float *b, const float *vin,
                           const float *zsrc, float *vout, int kbase, int kstep, int nplanes,
                           cudaStream_t s, int sms) {
     if (nplanes <= 0) return cudaSuccess;
     const int nstrips = (d.ny + kPersTY - 1) / kPersTY;
     const long ntiles = (long)nstrips * nplanes;
-    const long slots = (long)sms * kPersMinBlocks;
+    const long slots = pers_slots(d.nx, sms);
     const int grid = (int)(ntiles < slots ? ntiles : slots);
-    k_gs_rows_p<F, SPLIT, RES><<<grid, d.nx / 2, pers_floats(d.nx) * sizeof(float), s>>>(
-        d, f, b, vin, zsrc, vout, kbase, kstep, nplanes, nstrips);
+    k_gs_rows_p<OP, F, SPLIT, RES><<<grid, d.nx / 2, pers_floats(d.nx) * sizeof(float), s>>>(
+        d, op, b, vin, zsrc, vout, kbase, kstep, nplanes, nstrips);
     count_launch();
     return cudaGetLastError();
 }
 
-// sweep phase over the planes of parity par (1: odd planes 1 .. nz-1, 0:
-// even planes 2 .. nz-2)
-template <int F>
-cudaError_t rows_p_phase(const Dims &d, const Fine<float> &f, const float *b, const float *vin,
-                         const float *zsrc, float *vout, int par, cudaStream_t s, int split,
-                         int sms) {
-    const int kbase = par ? 1 : 2;
-    const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
-    return split ? launch_rows_p<F, true, false>(d, f, b, vin, zsrc, vout, kbase, 2, nplanes, s,
-                                                 sms)
-                 : launch_rows_p<F, false, false>(d, f, b, vin, zsrc, vout, kbase, 2, nplanes, s,
-                                                  sms);
+// one sweep: the planes of one parity, then the other (ascending: even
+// planes 2 .. nz-2 with colours 0-3, then odd planes 1 .. nz-1 with 4-7;
+// descending: odd planes with 7-4, then even planes with 3-0)
+template <class OP, bool SPLIT>
+cudaError_t rows_p_sweep(const Dims &d, const OP &op, const float *b, const float *vin,
+                         float *vout, bool descending, cudaStream_t s, int sms) {
+    const int ne = d.nz / 2 - 1, no = d.nz / 2;
+    cudaError_t e;
+    if (!descending) {
+        e = launch_rows_p<OP, 0, SPLIT, false>(d, op, b, vin, vin, vout, 2, 2, ne, s, sms);
+        if (e != cudaSuccess) return e;
+        return launch_rows_p<OP, 0, SPLIT, false>(d, op, b, vin, vout, vout, 1, 2, no, s, sms);
+    }
+    e = launch_rows_p<OP, 1, SPLIT, false>(d, op, b, vin, vin, vout, 1, 2, no, s, sms);
+    if (e != cudaSuccess) return e;
+    return launch_rows_p<OP, 1, SPLIT, false>(d, op, b, vin, vout, vout, 2, 2, ne, s, sms);
 }
 
-// whether the persistent kernel takes this grid and these arrays; sms set
-bool rows_p_ok(const Dims &d, const void *a, const void *b, const void *c, int &sms) {
+// whether the persistent kernel takes this grid; sms set
+bool rows_p_shape(const Dims &d, int &sms) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     sms = (dev >= 0 && dev < 64) ? g_sms[dev] : 0;
+    return sms > 0 && d.nx % 64 == 0 && d.nx <= kPersMaxNx && d.ny >= kPersR;
+}
+// ... and these arrays (16-byte aligned for the copies)
+bool rows_p_ok(const Dims &d, const void *a, const void *b, const void *c, int &sms) {
     const bool aligned = (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15) == 0;
-    return sms > 0 && aligned && d.nx % 64 == 0 && d.nx <= kPersMaxNx && d.ny >= kPersR;
+    return rows_p_shape(d, sms) && aligned;
 }
 
 }  // namespace
@@ -599,12 +764,14 @@ cudaError_t smoother_init() {
     SET((k_gs_rows<kRowsTY, 0, true>), smem)
     SET((k_gs_rows<kRowsTY, 1, false>), smem)
     SET((k_gs_rows<kRowsTY, 1, true>), smem)
-    SET((k_gs_rows_p<0, false, false>), smem_p)
-    SET((k_gs_rows_p<0, true, false>), smem_p)
-    SET((k_gs_rows_p<1, false, false>), smem_p)
-    SET((k_gs_rows_p<1, true, false>), smem_p)
-    SET((k_gs_rows_p<0, false, true>), smem_p)
-    SET((k_gs_rows_p<0, true, true>), smem_p)
+    SET((k_gs_rows_p<FineRowsOp, 0, false, false>), smem_p)
+    SET((k_gs_rows_p<FineRowsOp, 0, true, false>), smem_p)
+    SET((k_gs_rows_p<FineRowsOp, 1, false, false>), smem_p)
+    SET((k_gs_rows_p<FineRowsOp, 1, true, false>), smem_p)
+    SET((k_gs_rows_p<FineRowsOp, 0, false, true>), smem_p)
+    SET((k_gs_rows_p<FineRowsOp, 0, true, true>), smem_p)
+    SET((k_gs_rows_p<CoarseRowsOp, 0, false, false>), smem_p)
+    SET((k_gs_rows_p<CoarseRowsOp, 1, false, false>), smem_p)
 #undef SET
     return cudaSuccess;
 }
@@ -615,18 +782,13 @@ cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float 
                                const float *vin, float *vout, bool descending, cudaStream_t s,
                                int split) {
     int sms = 0;
-    cudaError_t e;
     if (rows_p_ok(d, b, vin, vout, sms)) {
-        if (!descending) {
-            e = rows_p_phase<0>(d, f, b, vin, vin, vout, 0, s, split, sms);
-            if (e != cudaSuccess) return e;
-            return rows_p_phase<0>(d, f, b, vin, vout, vout, 1, s, split, sms);
-        }
-        e = rows_p_phase<1>(d, f, b, vin, vin, vout, 1, s, split, sms);
-        if (e != cudaSuccess) return e;
-        return rows_p_phase<1>(d, f, b, vin, vout, vout, 0, s, split, sms);
+        const FineRowsOp op{f};
+        return split ? rows_p_sweep<FineRowsOp, true>(d, op, b, vin, vout, descending, s, sms)
+                     : rows_p_sweep<FineRowsOp, false>(d, op, b, vin, vout, descending, s, sms);
     }
     if (d.nx / 2 > kRowsMaxThreads) return cudaErrorNotSupported;
+    cudaError_t e;
     if (!descending) {
         e = rows_phase<0>(d, f, b, vin, vin, vout, 0, s, split);
         if (e != cudaSuccess) return e;
@@ -643,8 +805,31 @@ cudaError_t residual_fine_rows(const Dims &d, const Fine<float> &f, const float 
                                const float *x, float *r, cudaStream_t s, int split) {
     int sms = 0;
     if (!rows_p_ok(d, b, x, r, sms)) return cudaErrorNotSupported;
-    return split ? launch_rows_p<0, true, true>(d, f, b, x, x, r, 1, 1, d.nz - 1, s, sms)
-                 : launch_rows_p<0, false, true>(d, f, b, x, x, r, 1, 1, d.nz - 1, s, sms);
+    const FineRowsOp op{f};
+    return split ? launch_rows_p<FineRowsOp, 0, true, true>(d, op, b, x, x, r, 1, 1, d.nz - 1, s,
+                                                            sms)
+                 : launch_rows_p<FineRowsOp, 0, false, true>(d, op, b, x, x, r, 1, 1, d.nz - 1,
+                                                             s, sms);
+}
+
+// Coarse levels take the row strips only where they win (measured on GB300,
+// 27-point stencil, FMA-issue bound in every form): rows of 128 nodes and up
+// (128^3 level: 98 us a sweep against 103 us for eight colour launches); at
+// 64^3 the tile kernel is faster (35 against 49 us), and the coarse residual
+// stays one thread per node (55 against 59 us at 128^3).
+bool coarse_rows_fit(const Dims &d) {
+    int sms = 0;
+    return d.nx >= 128 && rows_p_shape(d, sms);
+}
+
+// coarse-level FP32 sweep with the persistent row-strip kernel (natural
+// column order), or cudaErrorNotSupported
+cudaError_t gs_sweep_coarse_rows(const Dims &d, const Coarse<float> &c, const float *b,
+                                 const float *vin, float *vout, bool descending, cudaStream_t s) {
+    int sms = 0;
+    if (d.nx < 128 || !rows_p_ok(d, b, vin, vout, sms)) return cudaErrorNotSupported;
+    const CoarseRowsOp op{c};
+    return rows_p_sweep<CoarseRowsOp, false>(d, op, b, vin, vout, descending, s, sms);
 }
 
 }  // namespace qsmg
