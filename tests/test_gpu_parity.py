@@ -374,7 +374,8 @@ def test_disc_wall_fill(kind):
 # multi-step runs use a 1.2 GPa preload: at 1.5 GPa the forward-Euler STZ
 # update overshoots in the hottest cells (2 mu D dt / sbar > 2) and diverges
 @pytest.mark.parametrize("preload,n,nz,steps", [(1.2e9, 16, None, 6), (0.0, 16, None, 4),
-                                                 (1.2e9, 24, 8, 5), (1.2e9, 32, None, 4)])
+                                                 (1.2e9, 24, 8, 5), (1.2e9, 32, None, 4),
+                                                 (1.2e9, 128, None, 2)])
 def test_qs_step_trajectory(preload, n, nz, steps):
     """Whole steps, warm-started solves, FP64: the GPU runs the oracle's cycle
     count each step (tol = 0 with max_cycles = oracle cycles)."""
@@ -416,3 +417,39 @@ def test_qs_step_mixed_tracks_fp64():
         assert st == 0 and s.rel_resid <= 1e-10
         ev, es = rel(c(vg), v), rel(c(sg), sig)
         assert ev <= 1e-6 and es <= 1e-6, (k, ev, es)
+
+
+def test_fullsize_bench_step_256():
+    """The bench's own configuration at full size: 256^3 cells, STZ-active
+    preload, mixed precision, the bench's solver options, one warm-started
+    step on the GPU.  The oracle then recomputes, from the same starting
+    state, the intermediate stress, the right-hand side and the walls, and
+    checks the GPU's velocity against its own operator (relative residual
+    within the tolerance, lifted as in the stopping rule), its stress
+    correction from that velocity and its chi update."""
+    import bench
+    w = bench.workload(256)
+    v, sig, chi, t = w.initial_state()
+    shape = (w.nx, w.ny, w.nz)
+    vg, sg, cg = g(v), g(sig), g(chi)
+    state = make_state(vg, sg, cg, t)
+    ctx = Context(*shape, w.h, I.TABLE1["K"], w.mu, bc=w.bc_values(), stz=w.stz,
+                  precision=MG_MIXED, max_cycles=100, inner_cycles=bench.INNER)
+    st, s = ctx.step(state, w.dt, bench.TOL)
+    assert st == 0 and s.rel_resid <= bench.TOL
+    ctx.close()
+    p = O.STZ(**w.stz)
+    bc = O.BC(**w.bc_values())
+    ss, D, sb = O.stress_star(v, sig, chi, w.h, w.dt, MU, p)
+    b = O.div_rhs(ss, w.h, w.dt, MU)
+    vn = c(vg)
+    vw = v.copy()
+    O.wall_fill(vw, w.h, bc, t + w.dt)
+    assert np.array_equal(vn[:, [0, w.nz]], vw[:, [0, w.nz]])
+    S = O.fine_stencil(LAM, MU)
+    v0 = vn.copy()
+    v0[:, 1:w.nz] = 0.0
+    rel_resid = np.sqrt(O.norm2(O.residual(S, b, vn)) / O.norm2(O.residual(S, b, v0)))
+    assert rel_resid <= 2.0 * bench.TOL, rel_resid
+    assert rel(c(sg), O.stress_final(vn, ss, w.h, w.dt, LAM, MU)) <= 1e-11
+    assert rel(c(cg), O.chi_update(sig, chi, D, sb, w.h, w.dt, p)) <= 1e-12
