@@ -64,8 +64,10 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<double> &c, const doubl
 cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float *b, float *x,
                              int colour, cudaStream_t s);
 
-// one-time kernel attribute set-up of the sweeps (call before any capture)
+// one-time kernel attribute set-up of the sweeps (call before any capture);
+// plane_init: that of the whole-plane coarse sweep (called by smoother_init)
 cudaError_t smoother_init();
+cudaError_t plane_init();
 // FP32 finest-level residual with the persistent row-strip kernel;
 // cudaErrorNotSupported when the grid or the arrays do not suit it
 cudaError_t residual_fine_rows(const Dims &d, const Fine<float> &f, const float *b,

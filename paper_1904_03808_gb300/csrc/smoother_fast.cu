@@ -359,7 +359,124 @@ cudaError_t sweep(const Dims &d, const Op &op, const T *b, const T *vin, T *vout
 }
 
 
+// ------------------------------------------------------------------------
+// Whole-plane phase kernel for small coarse levels (planes of at most
+// kPlaneMax nodes): one CTA per plane of the phase's parity holds the plane,
+// its two z-neighbour planes and its right-hand side in shared memory
+// ([component][ny][nx] each, 48 KB at 32 x 32), folds the z-neighbour terms
+// into the right-hand side once, and runs the 4 in-plane colour passes on
+// shared memory only, with periodic x, y indexing (no halo: the plane is
+// whole).  The tile kernel, whose 72 x 20 window wraps several times around
+// such small planes, spends ~15 us a launch on latency at these sizes.
+constexpr int kPlaneMax = 1024;
+constexpr int kPlaneThreads = 256;
+
+template <int F>
+__global__ void __launch_bounds__(kPlaneThreads)
+    k_gs_plane(Dims d, Coarse<float> c, const float *__restrict__ b, const float *__restrict__ vin,
+               const float *__restrict__ zsrc, float *__restrict__ vout, int kbase) {
+    extern __shared__ __align__(16) float smp[];
+    const int nx = d.nx, ny = d.ny, np = nx * ny;
+    const long ps = (long)np, cs = d.cs;
+    float *P = smp, *Lz = smp + 3 * np, *Hz = smp + 6 * np, *Rr = smp + 9 * np;
+    const int k = 2 * blockIdx.x + kbase;
+    for (int e = threadIdx.x; e < 3 * np; e += blockDim.x) {
+        const int a = e / np, m = e - a * np;
+        P[e] = vin[a * cs + k * ps + m];
+        Lz[e] = zsrc[a * cs + (k - 1) * ps + m];
+        Hz[e] = zsrc[a * cs + (k + 1) * ps + m];
+        Rr[e] = b[a * cs + k * ps + m];
+    }
+    __syncthreads();
+    // fold the z-neighbour blocks (dz = -1, +1) into the right-hand side
+    for (int m = threadIdx.x; m < np; m += blockDim.x) {
+        const int j = m / nx, i = m - j * nx;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int dz = -1; dz <= 1; dz += 2) {
+            const float *Z = dz < 0 ? Lz : Hz;
+#pragma unroll
+            for (int dy = -1; dy <= 1; dy++) {
+                int jj = j + dy;
+                jj = jj < 0 ? jj + ny : (jj >= ny ? jj - ny : jj);
+#pragma unroll
+                for (int dx = -1; dx <= 1; dx++) {
+                    int ii = i + dx;
+                    ii = ii < 0 ? ii + nx : (ii >= nx ? ii - nx : ii);
+                    const int q = jj * nx + ii;
+                    const float u0 = Z[q], u1 = Z[np + q], u2 = Z[2 * np + q];
+                    const float *S = c.S + ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) * 9;
+                    s0 += S[0] * u0 + S[1] * u1 + S[2] * u2;
+                    s1 += S[3] * u0 + S[4] * u1 + S[5] * u2;
+                    s2 += S[6] * u0 + S[7] * u1 + S[8] * u2;
+                }
+            }
+        }
+        Rr[m] -= s0;
+        Rr[np + m] -= s1;
+        Rr[2 * np + m] -= s2;
+    }
+    __syncthreads();
+    // colours (F,F), (1-F,F), (F,1-F), (1-F,1-F) in (x, y) parity
+    const int hx = nx >> 1, nh = np >> 2;
+#pragma unroll 1
+    for (int pass = 0; pass < 4; pass++) {
+        const int pi = (pass & 1) ? 1 - F : F, pj = (pass & 2) ? 1 - F : F;
+        for (int t = threadIdx.x; t < nh; t += blockDim.x) {
+            const int jh = t / hx, i = 2 * (t - jh * hx) + pi, j = 2 * jh + pj;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+            for (int dy = -1; dy <= 1; dy++) {
+                int jj = j + dy;
+                jj = jj < 0 ? jj + ny : (jj >= ny ? jj - ny : jj);
+#pragma unroll
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (dy == 0 && dx == 0) continue;
+                    int ii = i + dx;
+                    ii = ii < 0 ? ii + nx : (ii >= nx ? ii - nx : ii);
+                    const int q = jj * nx + ii;
+                    const float u0 = P[q], u1 = P[np + q], u2 = P[2 * np + q];
+                    const float *S = c.S + (9 + (dy + 1) * 3 + (dx + 1)) * 9;
+                    s0 += S[0] * u0 + S[1] * u1 + S[2] * u2;
+                    s1 += S[3] * u0 + S[4] * u1 + S[5] * u2;
+                    s2 += S[6] * u0 + S[7] * u1 + S[8] * u2;
+                }
+            }
+            const int m = j * nx + i;
+            const float f0 = Rr[m] - s0, f1 = Rr[np + m] - s1, f2 = Rr[2 * np + m] - s2;
+            P[m] = c.Dinv[0] * f0 + c.Dinv[1] * f1 + c.Dinv[2] * f2;
+            P[np + m] = c.Dinv[3] * f0 + c.Dinv[4] * f1 + c.Dinv[5] * f2;
+            P[2 * np + m] = c.Dinv[6] * f0 + c.Dinv[7] * f1 + c.Dinv[8] * f2;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < 3 * np; e += blockDim.x) {
+        const int a = e / np, m = e - a * np;
+        vout[a * cs + k * ps + m] = P[e];
+    }
+}
+
+template <int F>
+cudaError_t launch_plane(const Dims &d, const Coarse<float> &c, const float *b, const float *vin,
+                         const float *zsrc, float *vout, int par, cudaStream_t s) {
+    const int kbase = par ? 1 : 2;
+    const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
+    if (nplanes <= 0) return cudaSuccess;
+    const size_t smem = 12 * (size_t)d.nx * d.ny * sizeof(float);
+    k_gs_plane<F><<<nplanes, kPlaneThreads, smem, s>>>(d, c, b, vin, zsrc, vout, kbase);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t plane_init() {
+    const int smem = (int)(12 * (size_t)kPlaneMax * sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(k_gs_plane<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gs_plane<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
 
 // one 8-colour sweep vin -> vout (vout's wall planes must hold the walls)
 cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,
@@ -374,6 +491,18 @@ cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float
 
 cudaError_t gs_sweep_coarse_tiled(const Dims &d, const Coarse<float> &c, const float *b,
                                   const float *vin, float *vout, bool descending, cudaStream_t s) {
+    if ((long)d.nx * d.ny <= kPlaneMax) {
+        // whole planes in shared memory
+        cudaError_t e;
+        if (!descending) {
+            e = launch_plane<0>(d, c, b, vin, vin, vout, 0, s);
+            if (e != cudaSuccess) return e;
+            return launch_plane<0>(d, c, b, vin, vout, vout, 1, s);
+        }
+        e = launch_plane<1>(d, c, b, vin, vin, vout, 1, s);
+        if (e != cudaSuccess) return e;
+        return launch_plane<1>(d, c, b, vin, vout, vout, 0, s);
+    }
     // whole-row strips where the rows fit (smoother_rows.cu)
     const cudaError_t e = gs_sweep_coarse_rows(d, c, b, vin, vout, descending, s);
     if (e != cudaErrorNotSupported) return e;
