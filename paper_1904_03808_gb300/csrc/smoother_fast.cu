@@ -367,9 +367,12 @@ cudaError_t sweep(const Dims &d, const Op &op, const T *b, const T *vin, T *vout
 // into the right-hand side once, and runs the 4 in-plane colour passes on
 // shared memory only, with periodic x, y indexing (no halo: the plane is
 // whole).  The tile kernel, whose 72 x 20 window wraps several times around
-// such small planes, spends ~15 us a launch on latency at these sizes.
+// such small planes, spends ~15-17 us a launch on latency at these sizes;
+// this kernel takes 10.7 us at 32 x 32 (one thread per node) and 6.4-6.7 us
+// at 16 x 16 and 8 x 8 (measured on GB300).  At 64 x 64 it loses to the tile
+// kernel (27.7 against 18 us: one CTA per plane leaves most SMs idle).
 constexpr int kPlaneMax = 1024;
-constexpr int kPlaneThreads = 256;
+constexpr int kPlaneThreads = 1024;  // at most; one per node of the plane
 
 template <int F>
 __global__ void __launch_bounds__(kPlaneThreads)
@@ -463,7 +466,9 @@ cudaError_t launch_plane(const Dims &d, const Coarse<float> &c, const float *b, 
     const int nplanes = par ? d.nz / 2 : d.nz / 2 - 1;
     if (nplanes <= 0) return cudaSuccess;
     const size_t smem = 12 * (size_t)d.nx * d.ny * sizeof(float);
-    k_gs_plane<F><<<nplanes, kPlaneThreads, smem, s>>>(d, c, b, vin, zsrc, vout, kbase);
+    const int np = d.nx * d.ny;
+    const int threads = np < kPlaneThreads ? ((np + 31) / 32) * 32 : kPlaneThreads;
+    k_gs_plane<F><<<nplanes, threads, smem, s>>>(d, c, b, vin, zsrc, vout, kbase);
     count_launch();
     return cudaGetLastError();
 }
