@@ -866,7 +866,8 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         return MG_ERR_ARG;
     }
     {
-        const cudaError_t e = smoother_init();
+        cudaError_t e = smoother_init();
+        if (e == cudaSuccess) e = plane_init();
         if (e != cudaSuccess) {
             set_err("mg_setup: %s", cudaGetErrorString(e));
             delete ctx;

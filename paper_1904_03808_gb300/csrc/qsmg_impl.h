@@ -64,8 +64,8 @@ cudaError_t gs_colour_coarse(const Dims &d, const Coarse<double> &c, const doubl
 cudaError_t gs_colour_coarse(const Dims &d, const Coarse<float> &c, const float *b, float *x,
                              int colour, cudaStream_t s);
 
-// one-time kernel attribute set-up of the sweeps (call before any capture);
-// plane_init: that of the whole-plane coarse sweep (called by smoother_init)
+// one-time kernel attribute set-up of the sweeps (call before any capture):
+// smoother_init for the row-strip kernels, plane_init for the whole-plane one
 cudaError_t smoother_init();
 cudaError_t plane_init();
 // FP32 finest-level residual with the persistent row-strip kernel;

@@ -750,7 +750,6 @@ cudaError_t smoother_init() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if ((e = plane_init()) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) {
         e = cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
