@@ -252,3 +252,45 @@ def test_printed_constants():
     for key in ("K", "mu", "rho", "sY", "tau0", "eps0", "c0", "Delta_K", "T", "chi_inf", "ez_K"):
         assert I.TABLE1[key] == g[key]["value"], key
     assert abs(I.TABLE1["Omega"] - g["Omega_A3"]["value"] * 1e-30) < 1e-40
+
+
+def test_chi_diffusion_second_order_at_the_z_walls():
+    """Fields linear in z -- chi = 620 + 30 z/Z and sigma_xz = 1.5 + 0.2 z/Z GPa,
+    uniform in x and y, above yield -- continue exactly by linear
+    extrapolation, so the ghost cells beyond the walls (extrapolated chi and
+    sigma, D^pl taken from the extrapolated values: reading of section 4) give
+    the first and last cells the stencil of an interior cell.  The discrete
+    l^2 d/dz(D dchi/dz) must then converge at second order to the closed form
+    l^2 chi_z dD/dz in every cell, the wall cells included; a wrong ghost
+    value or index, or a ghost D^pl taken from the unextrapolated fields,
+    leaves an O(1) or O(h) error there.  dD/dz is a fine 5-point difference of
+    the pointwise rate D(sbar(z), chi(z)) along the exact fields."""
+    p = stz(l=1e-4)
+    dt = 1e-5
+    errs, errs_wall = [], []
+    for n in (16, 32, 64):
+        h = 1e-4
+        Z = n * h
+        z = (np.arange(n) + 0.5) * h
+        chi_f = lambda zz: 620.0 + 30.0 * zz / Z  # noqa: E731
+        sig_f = lambda zz: 1.5e9 + 0.2e9 * zz / Z  # noqa: E731
+        chi = np.broadcast_to(chi_f(z)[:, None, None], (n, 4, 4)).copy()
+        sig = np.zeros((6, n, 4, 4))
+        sig[4] = sig_f(z)[:, None, None]
+        v = np.zeros((3, n + 1, 4, 4))
+        ss, D, sb = O.stress_star(v, sig, chi, h, dt, MU, p)
+        new = O.chi_update(sig, chi, D, sb, h, dt, p)
+        growth = dt / p.c0 * (2 * D * sb / p.sY) * (p.chi_inf - chi)
+        term = ((new - chi - growth) * p.c0 / dt)[:, 1, 1]
+        # sbar of a pure xz shear is |sigma_xz|
+        rate = lambda zz: O.dpl(p, sig_f(zz), chi_f(zz))  # noqa: E731
+        dlt = Z * 1e-4
+        want = np.array([p.l ** 2 * (30.0 / Z) *
+                         (-rate(zz + 2 * dlt) + 8 * rate(zz + dlt) - 8 * rate(zz - dlt) +
+                          rate(zz - 2 * dlt)) / (12 * dlt) for zz in z])
+        assert np.allclose(D[:, 1, 1], [rate(zz) for zz in z], rtol=1e-12, atol=0)
+        err = np.abs(term - want) / np.abs(want).max()
+        errs.append(err.max())
+        errs_wall.append(max(err[0], err[-1]))
+    for e in (errs, errs_wall):
+        assert abs(np.log2(e[0] / e[1]) - 2) < 0.2 and abs(np.log2(e[1] / e[2]) - 2) < 0.2, e
