@@ -164,37 +164,53 @@ __global__ void k_chi_update(StepParams p, StzConst c, const double *__restrict_
 
 // b = (h^2/(mu dt)) div sigma* at interior corners; the corner derivative is
 // Eq. (31) shifted by half a cell: cells (i-1..i, j-1..j, k-1..k)
+// corner divergence, marching up one (i, j) corner column over kDivChunk
+// corner planes: each cell layer's contributions -- x-differences of
+// sigma_a0, y-differences of sigma_a1 and the layer sum of sigma_a2 over the
+// 2 x 2 cells around the column -- are formed once and shared by the corners
+// below and above the layer (FP64 is add-bound here: about 42 adds a corner
+// instead of 72)
+constexpr int kDivChunk = 16;
+
+struct DivLayer {
+    double X[3], Y[3], Z[3];
+};
+
+__device__ __forceinline__ DivLayer div_layer(const double *__restrict__ ss, long nc, long base,
+                                              long rj0, long rj1, int im, int i) {
+    // stored component of sigma_ab: xx, yy, zz, yz, xz, xy
+    const int comp[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    DivLayer L;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double *fx = ss + comp[a][0] * nc + base, *fy = ss + comp[a][1] * nc + base,
+                     *fz = ss + comp[a][2] * nc + base;
+        L.X[a] = (fx[rj0 + i] - fx[rj0 + im]) + (fx[rj1 + i] - fx[rj1 + im]);
+        L.Y[a] = (fy[rj1 + im] - fy[rj0 + im]) + (fy[rj1 + i] - fy[rj0 + i]);
+        L.Z[a] = (fz[rj0 + im] + fz[rj0 + i]) + (fz[rj1 + im] + fz[rj1 + i]);
+    }
+    return L;
+}
+
 __global__ void k_div_rhs(StepParams p, const double *__restrict__ ss, double *__restrict__ b,
                           double scale) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    int i, j, k;
-    if (!cell_ijk(nx, ny, i, j, k)) return;
-    k += 1;  // interior corner planes 1..nz-1
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const int k0 = 1 + blockIdx.z * kDivChunk;
+    const int k1 = k0 + kDivChunk < nz ? k0 + kDivChunk : nz;  // corners k0 .. k1-1
     const int im = i ? i - 1 : nx - 1, jm = j ? j - 1 : ny - 1;
     const long nc = (long)nx * ny * nz, pl = (long)nx * ny;
-    // the 8 surrounding cells c[dk][dj][di], d = 0 is the lower neighbour
-    const long kb0 = (long)(k - 1) * pl, kb1 = (long)k * pl;
     const long rj0 = (long)jm * nx, rj1 = (long)j * nx;
-    const long cc[2][2][2] = {{{kb0 + rj0 + im, kb0 + rj0 + i}, {kb0 + rj1 + im, kb0 + rj1 + i}},
-                              {{kb1 + rj0 + im, kb1 + rj0 + i}, {kb1 + rj1 + im, kb1 + rj1 + i}}};
-    // stored component of sigma_ab
-    const int comp[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
     const long cs = (long)(nz + 1) * pl;
-    const long node = (long)k * pl + (long)j * nx + i;
+    DivLayer lo = div_layer(ss, nc, (long)(k0 - 1) * pl, rj0, rj1, im, i);
+    for (int k = k0; k < k1; k++) {
+        const DivLayer hi = div_layer(ss, nc, (long)k * pl, rj0, rj1, im, i);
+        const long node = (long)k * pl + (long)j * nx + i;
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const double *fx = ss + comp[a][0] * nc, *fy = ss + comp[a][1] * nc,
-                     *fz = ss + comp[a][2] * nc;
-        double s = 0.0;
-#pragma unroll
-        for (int u = 0; u < 2; u++)
-#pragma unroll
-            for (int w = 0; w < 2; w++) {
-                s += fx[cc[u][w][1]] - fx[cc[u][w][0]];
-                s += fy[cc[u][1][w]] - fy[cc[u][0][w]];
-                s += fz[cc[1][u][w]] - fz[cc[0][u][w]];
-            }
-        b[a * cs + node] = scale * s;
+        for (int a = 0; a < 3; a++)
+            b[a * cs + node] = scale * ((lo.X[a] + hi.X[a]) + (lo.Y[a] + hi.Y[a]) + (hi.Z[a] - lo.Z[a]));
+        lo = hi;
     }
 }
 
@@ -281,7 +297,8 @@ cudaError_t div_rhs(const StepParams &p, const double *sig_star, double *b, cuda
         e = cudaMemsetAsync(b + a * cs + (long)p.nz * pl, 0, pl * sizeof(double), s);
         if (e != cudaSuccess) return e;
     }
-    k_div_rhs<<<cell_grid(p.nx, p.ny, p.nz - 1), kBlock, 0, s>>>(p, sig_star, b, scale);
+    k_div_rhs<<<cell_grid(p.nx, p.ny, (p.nz - 1 + kDivChunk - 1) / kDivChunk), kBlock, 0, s>>>(
+        p, sig_star, b, scale);
     count_launch();
     return cudaGetLastError();
 }
