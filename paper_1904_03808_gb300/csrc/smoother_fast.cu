@@ -12,9 +12,13 @@
 // same neighbour values), with v read and written about twice per sweep
 // instead of eight times.
 //
-// The finest level, when its rows hold at most 512 nodes, takes the row-strip
-// kernels of smoother_rows.cu.  Otherwise (wider finest rows, and the coarse
-// levels), inside one plane a CTA owns a TX x TY tile and stages a window of that plane
+// Which kernel implements a phase (FP32): rows of 64, 128 or 256 nodes take
+// the persistent row-strip kernel of smoother_rows.cu (finest level, and
+// coarse levels of rows >= 128 nodes), other finest rows of up to 512 nodes
+// its per-tile row-strip kernel; coarse planes of at most 32 x 32 nodes take
+// the whole-plane kernel further below.  Everything else -- wider finest
+// rows, the 64^3-like coarse levels -- takes the tile kernel: inside one
+// plane a CTA owns a TX x TY tile and stages a window of that plane
 // with a halo of HX columns and HY rows in shared memory (17 KB in FP32); the
 // z-neighbour planes and the right-hand side, which the phase only reads,
 // come through the read-only cache.  The same kernel
