@@ -294,3 +294,57 @@ def test_chi_diffusion_second_order_at_the_z_walls():
         errs_wall.append(max(err[0], err[-1]))
     for e in (errs, errs_wall):
         assert abs(np.log2(e[0] / e[1]) - 2) < 0.2 and abs(np.log2(e[1] / e[2]) - 2) < 0.2, e
+
+
+def _linear_velocity(L, nx, ny, nz, h):
+    """Corner velocities v_a = sum_b L_ab x_b (x_b = index * h)."""
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny), np.arange(nx), indexing="ij")
+    X = [i * h, j * h, k * h]
+    return np.stack([sum(L[a, b] * X[b] for b in range(3)) for a in range(3)])
+
+
+def test_stress_predictor_under_linear_velocity():
+    """Below yield (D^pl = 0) and for a velocity linear in x, y, z, every
+    cell away from the periodic wrap sees the constant gradient L, and Eq. 27
+    gives sigma* = sigma + dt (L sigma + sigma L^T - tr(L) sigma) for a
+    general L and a general symmetric sigma (all six components)."""
+    rng = np.random.default_rng(12)
+    nx, ny, nz, h, dt = 7, 6, 5, 1e-3, 1e-2
+    L = rng.normal(size=(3, 3))
+    v = _linear_velocity(L, nx, ny, nz, h)
+    S = rng.normal(size=(3, 3)) * 1e8
+    S = 0.5 * (S + S.T)  # ~0.1 GPa: far below the 0.85 GPa yield stress
+    comp = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    sig = np.stack([np.full((nz, ny, nx), S[a, b]) for a, b in comp])
+    chi = np.full((nz, ny, nx), 600.0)
+    ss, D, _ = O.stress_star(v, sig, chi, h, dt, MU, stz())
+    assert np.all(D == 0.0)
+    want = S + dt * (L @ S + S @ L.T - np.trace(L) * S)
+    for q, (a, b) in enumerate(comp):
+        got = ss[q][:, : ny - 1, : nx - 1]  # cells whose corners do not wrap
+        assert np.allclose(got, want[a, b], rtol=0, atol=1e-12 * np.abs(S).max()), (a, b)
+
+
+def test_stress_predictor_rotation_keeps_invariants():
+    """A rigid rotation rate (L = W skew, tr W = 0) leaves tr(sigma*) =
+    tr(sigma) to rounding and changes |sigma|_F^2 only at second order in dt
+    (the rate W sigma - sigma W is orthogonal to sigma)."""
+    rng = np.random.default_rng(13)
+    nx, ny, nz, h = 6, 6, 4, 1e-3
+    w = rng.normal(size=3)
+    W = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+    v = _linear_velocity(W, nx, ny, nz, h)
+    S = rng.normal(size=(3, 3)) * 1e8
+    S = 0.5 * (S + S.T)
+    comp = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    sig = np.stack([np.full((nz, ny, nx), S[a, b]) for a, b in comp])
+    chi = np.full((nz, ny, nx), 600.0)
+    for dt in (1e-2, 5e-3):
+        ss, _, _ = O.stress_star(v, sig, chi, h, dt, MU, stz())
+        c = (slice(None), slice(0, ny - 1), slice(0, nx - 1))
+        tr0, tr1 = np.trace(S), ss[0][c] + ss[1][c] + ss[2][c]
+        assert np.allclose(tr1, tr0, rtol=0, atol=1e-13 * np.abs(S).max())
+        f2 = ss[0][c] ** 2 + ss[1][c] ** 2 + ss[2][c] ** 2 + 2 * (
+            ss[3][c] ** 2 + ss[4][c] ** 2 + ss[5][c] ** 2)
+        R = W @ S - S @ W
+        assert np.allclose(f2 - np.sum(S * S), dt ** 2 * np.sum(R * R), rtol=1e-6, atol=0)
