@@ -100,8 +100,8 @@ typedef struct {
  *                 0 picks the count per step from the FP64 residual and the
  *                 observed V-cycle contraction.
  *   flags         0 or an OR of: MG_FLAG_COLOUR_PASSES runs FP32 sweeps as
- *                 eight colour launches instead of the tiled two-phase
- *                 kernels; MG_FLAG_NO_GRAPH issues the FP32 inner cycles as
+ *                 eight colour launches instead of the two-phase kernels
+ *                 (row strips, whole planes, tiles); MG_FLAG_NO_GRAPH issues the FP32 inner cycles as
  *                 plain launches instead of replaying a CUDA graph captured
  *                 at their first use (same arithmetic; kept for comparison).
  */
@@ -190,7 +190,8 @@ const char *mg_last_error(void);
 
 /* ------------------------------------------------------------------ */
 /* Component entry points (the same kernels the solve and step use),   */
-/* exposed for parity tests against the oracle.  Device pointers, FP64.  */
+/* exposed for parity tests against the oracle.  Device pointers, FP64  */
+/* unless stated.  Errors: MG_ERR_ARG (null array, bad level), MG_ERR_CUDA. */
 /* ------------------------------------------------------------------ */
 
 /* number of levels, and the cell dimensions of one level (dims[3]) */
