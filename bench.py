@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--sweep-only", action="store_true")
     ap.add_argument("--disc", action="store_true")
     ap.add_argument("--dt-ts", type=float, default=2.0e4)
+    ap.add_argument("--kind", type=int, default=1, choices=[1, 2, 3],
+                    help="disc walls: 1 top only, 2 both faces together, 3 counter-rotating")
     ap.add_argument("--chi", default="450,15,5",
                     help="disc chi0 recipe: mean K, std K, correlation length in cells")
     ap.add_argument("--nz", type=int, default=0)
@@ -78,7 +80,7 @@ def run_disc(args):
     K = args.steps
     cm, cs_, clc = (float(x) for x in args.chi.split(","))
     t_setup = time.time()
-    w = I.Workload(n, steps=K, kind=1, chi_mean=cm, chi_std=cs_, lc_cells=clc, seed=5,
+    w = I.Workload(n, steps=K, kind=args.kind, chi_mean=cm, chi_std=cs_, lc_cells=clc, seed=5,
                    dt_ts=args.dt_ts)
     w.omega = 2.0 * math.pi / (1.0e8 * w.ts)
     v0, s0, c0, t0 = w.initial_state()
@@ -130,7 +132,7 @@ def run_disc(args):
     tail = ok_rows[1:] if len(ok_rows) > 1 else ok_rows
     mix = statistics.mean(r["mixed_ms"] for r in tail)
     f64 = statistics.mean(r["fp64_ms"] for r in tail)
-    return {"mode": "disc", "grid": [n, n, n], "steps": K, "dt_ts": args.dt_ts,
+    return {"mode": "disc", "kind": args.kind, "grid": [n, n, n], "steps": K, "dt_ts": args.dt_ts,
             "omega_rad_s": w.omega, "R_over_L": w.R,
             "chi0": "%g K / %g K / l_c = %g cells, seed 5" % (cm, cs_, clc),
             "mixed_ms_per_step": mix, "fp64_ms_per_step": f64, "speedup_mixed": f64 / mix,

@@ -404,6 +404,40 @@ def test_qs_step_trajectory(preload, n, nz, steps):
         ctx.close()
 
 
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_qs_step_disc_walls_trajectory(kind):
+    """Whole FP64 steps under the friction-welding walls of section 5 (kind 1:
+    top disc rotating, bottom fixed; 2: both faces rotating together; 3:
+    counter-rotating), chi0 with the section-5 recipe and a 1.2 GPa sigma_xz
+    preload so that the STZ rate and the chi update are active, against the
+    oracle with its cycle count each step."""
+    import math
+    n = 16
+    w = I.Workload(n, steps=10, kind=kind, chi_mean=450.0, chi_std=15.0, lc_cells=2.0, seed=5,
+                   dt_ts=2.0e3, preload=1.2e9)
+    w.omega = 2.0 * math.pi / (1.0e8 * w.ts)
+    v, sig, chi, t = w.initial_state()
+    shape = (w.nx, w.ny, w.nz)
+    mg = O.MG(*shape, LAM, MU)
+    p = O.STZ(**w.stz)
+    bc = O.BC(**w.bc_values())
+    vg, sg, cg = g(v), g(sig), g(chi)
+    state = make_state(vg, sg, cg, t)
+    for k in range(3):
+        st, cyc, _ = O.qs_step(mg, v, sig, chi, w.h, w.dt, LAM, MU, p, bc, t, tol=1e-10,
+                               max_cycles=100)
+        assert st == 0
+        t += w.dt
+        ctx = ctx_for(shape, w=w, max_cycles=cyc)
+        ctx.step(state, w.dt, tol=0.0)
+        ctx.close()
+        assert rel(c(vg), v) <= TOL64, (kind, k)
+        assert rel(c(sg), sig) <= TOL64, (kind, k)
+        assert rel(c(cg), chi) <= TOL64, (kind, k)
+    assert np.abs(v[:, w.nz]).max() > 0  # the top wall moved
+    assert (np.abs(v[:, 0]).max() > 0) == (kind != 1)  # the bottom one with kinds 2, 3
+
+
 def test_qs_step_mixed_tracks_fp64():
     w, v, sig, chi, t = _stz_state(32, preload=1.2e9)
     shape = (w.nx, w.ny, w.nz)
