@@ -16,10 +16,12 @@ Prints one JSON line (rank 0).
 times K finest-level FP32 sweeps alone (two per call, random data, one GPU)
 and prints their mean duration; the small case for kernel profiles.
 
-        python bench.py --disc [--n 512] [--steps 20]
-friction-welding disc workload (section 5): n^3 cells, bottom wall fixed, top
-wall rotating inside radius R = L/3 (omega = 2 pi / (1e8 t_s)), dt = 2e4 t_s,
-chi0 with correlation length 8 cells; mixed and FP64 run in lockstep from the
+        python bench.py --disc [--n 512] [--nz NZ] [--kind 1|2|3] [--steps 20]
+friction-welding disc workload (section 5): n x n x nz cells (nz = n by
+default; section 5 prints a 768 x 768 x 384 grid), the top wall rotating
+inside radius R = L/3 (omega = 2 pi / (1e8 t_s)) and the bottom one fixed
+(kind 1), rotating with it (2) or against it (3); dt = 2e4 t_s, chi0 450 K /
+15 K / correlation length 5 cells; mixed and FP64 run in lockstep from the
 same state; per-step device times and the mixed run's velocity and stress
 error against the FP64 run.
 """
@@ -81,7 +83,7 @@ def run_disc(args):
     cm, cs_, clc = (float(x) for x in args.chi.split(","))
     t_setup = time.time()
     w = I.Workload(n, steps=K, kind=args.kind, chi_mean=cm, chi_std=cs_, lc_cells=clc, seed=5,
-                   dt_ts=args.dt_ts)
+                   dt_ts=args.dt_ts, nz=args.nz or None)
     w.omega = 2.0 * math.pi / (1.0e8 * w.ts)
     v0, s0, c0, t0 = w.initial_state()
     t_setup = time.time() - t_setup
@@ -132,7 +134,7 @@ def run_disc(args):
     tail = ok_rows[1:] if len(ok_rows) > 1 else ok_rows
     mix = statistics.mean(r["mixed_ms"] for r in tail)
     f64 = statistics.mean(r["fp64_ms"] for r in tail)
-    return {"mode": "disc", "kind": args.kind, "grid": [n, n, n], "steps": K, "dt_ts": args.dt_ts,
+    return {"mode": "disc", "kind": args.kind, "grid": [w.nx, w.ny, w.nz], "steps": K, "dt_ts": args.dt_ts,
             "omega_rad_s": w.omega, "R_over_L": w.R,
             "chi0": "%g K / %g K / l_c = %g cells, seed 5" % (cm, cs_, clc),
             "mixed_ms_per_step": mix, "fp64_ms_per_step": f64, "speedup_mixed": f64 / mix,

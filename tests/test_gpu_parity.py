@@ -66,11 +66,12 @@ def test_hierarchy_and_galerkin_tables(shape):
 
 
 @pytest.mark.parametrize("shape", [(64, 32, 32), (256, 32, 32), (128, 40, 32), (72, 40, 16),
-                                   (16, 8, 12), (512, 32, 32)])
+                                   (16, 8, 12), (512, 32, 32), (192, 24, 16), (384, 32, 32),
+                                   (768, 64, 64)])
 def test_residual32_every_level(shape):
     """FP32 residual of the mixed-precision V-cycles against the oracle's on
     the same (FP32-rounded) arrays: the persistent row-strip kernel on the
-    finest level for rows of 64/128/256 nodes with at least 9 rows (ragged
+    finest level for rows of 64/128/192/256 nodes with at least 9 rows (ragged
     strips at ny = 40), one thread per node otherwise, coarse levels."""
     rng = np.random.default_rng(11)
     ctx = ctx_for(shape, precision=MG_MIXED)
@@ -144,17 +145,17 @@ def test_smoother_fp32_fine_level(shape):
 
 @pytest.mark.parametrize("shape", [(72, 40, 16), (16, 8, 12), (8, 4, 2), (136, 72, 32), (64, 32, 32),
                                    (10, 16, 16), (1024, 64, 64), (256, 32, 32), (128, 40, 32),
-                                   (512, 32, 32)])
+                                   (512, 32, 32), (192, 24, 16), (384, 32, 32), (768, 64, 64)])
 @pytest.mark.parametrize("sweeps,descending", [(1, False), (2, False), (1, True), (3, True)])
 def test_tiled_fp32_sweep_equals_colour_passes(shape, sweeps, descending):
     """The tiled two-phase FP32 sweeps reproduce the eight colour launches on
     every smoothed level (ragged tiles, odd sweep counts, non-zero walls on the
-    finest level, both colour orders).  On the finest level rows of 64, 128
-    and 256 nodes take the persistent row-strip kernel, other rows of up to
-    512 nodes the per-tile row-strip kernel (136, 72 and 512 wide), wider rows
-    (1024) the tile kernel; coarse levels take the row-strip kernel (rows of
-    128 or 256 nodes, at least 9 rows), the whole-plane kernel (planes of at
-    most 32 x 32 nodes) or the tile kernel."""
+    finest level, both colour orders).  On the finest level rows of 64, 128,
+    192 and 256 nodes take the persistent row-strip kernel, other rows of up
+    to 512 nodes the per-tile row-strip kernel (136, 72, 384 and 512 wide),
+    wider rows (768, 1024) the tile kernel; coarse levels take the row-strip
+    kernel (rows of 128, 192 or 256 nodes, at least 9 rows), the whole-plane
+    kernel (planes of at most 32 x 32 nodes) or the tile kernel."""
     rng = np.random.default_rng(7)
     ctxs = [ctx_for(shape, precision=MG_MIXED, flags=f) for f in (0, 1)]
     nlev = ctxs[0].levels
