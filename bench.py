@@ -281,17 +281,28 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
+def code_digest(src: bytes) -> str:
+    """sha256 of a C/CUDA source with its // comments, trailing blanks and
+    empty lines removed: the digest changes with the code, not the comments."""
+    import hashlib
+    lines = []
+    for ln in src.decode().splitlines():
+        ln = ln.split("//", 1)[0].rstrip()
+        if ln:
+            lines.append(ln)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def traffic_per_sweep(n_nodes):
     """DRAM bytes per finest-level sweep from the committed ncu summary, scaled
-    by node count, or None when the smoother source changed since capture."""
+    by node count, or None when the smoother code changed since capture."""
     p = os.path.join(ROOT, "profiles", "smoother_traffic.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
-    import hashlib
     src = open(os.path.join(ROOT, "paper_1904_03808_gb300", "csrc", d["source"]), "rb").read()
-    if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+    if code_digest(src) != d["code_sha256"]:
         return None
     return d["dram_bytes_per_node_per_sweep"] * n_nodes
 

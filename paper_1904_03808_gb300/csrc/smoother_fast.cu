@@ -12,8 +12,8 @@
 // same neighbour values), with v read and written about twice per sweep
 // instead of eight times.
 //
-// Which kernel implements a phase (FP32): rows of 64, 128 or 256 nodes take
-// the persistent row-strip kernel of smoother_rows.cu (finest level, and
+// Which kernel implements a phase (FP32): rows of 64, 128, 192 or 256 nodes
+// take the persistent row-strip kernel of smoother_rows.cu (finest level, and
 // coarse levels of rows >= 128 nodes), other finest rows of up to 512 nodes
 // its per-tile row-strip kernel; coarse planes of at most 32 x 32 nodes take
 // the whole-plane kernel further below.  Everything else -- wider finest

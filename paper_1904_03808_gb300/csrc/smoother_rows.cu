@@ -8,7 +8,8 @@
 // z-neighbour planes), then the planes of the other parity (reading the
 // first phase's output).  Here a CTA owns whole rows of a plane, so the
 // periodic x direction needs no halo.  Two kernels:
-//   k_gs_rows_p  persistent, for rows of 64, 128 or 256 nodes: the rows of
+//   k_gs_rows_p  persistent, for rows of 64, 128, 192 or 256 nodes (a
+//                multiple of 64, at least 9 rows): the rows of
 //                each tile are copied into shared memory with cp.async while
 //                the other CTAs on the SM compute; templated on the operator
 //                (FineRowsOp, CoarseRowsOp) and, with RES, computing the
