@@ -37,3 +37,22 @@ def test_setup_rejects_bad_shapes_without_touching_the_gpu():
     assert L.mg_setup(ctypes.byref(g), ctypes.byref(m), None, None, ctypes.byref(bad), None,
                       ctypes.byref(out)) == binding.MG_ERR_ARG
     assert L.mg_solve(None, None, None, 1e-10, None) == binding.MG_ERR_ARG
+
+
+def test_setup_rejects_a_coarsest_level_beyond_the_dense_solve():
+    """Coarsening stops once a dimension would fall below 4 cells; the level
+    left must fit the dense coarsest solve (3072 unknowns).  A slender
+    768 x 768 x 192 grid stops at 24 x 24 x 6 (8640 unknowns) and 384 x 24 x 16
+    at 96 x 6 x 4 (5184): both are refused before any device work, with the
+    level named in the error string."""
+    L = binding.lib()
+    out = ctypes.c_void_p()
+    o = binding.mg_opts(0, 2, 2, 50, 4)
+    m = binding.mg_moduli(122e9, 37.4e9)
+    for shape, level in (((768, 768, 192), b"24x24x6"), ((384, 24, 16), b"96x6x4")):
+        g = binding.mg_grid(*shape, 1e-3)
+        st = L.mg_setup(ctypes.byref(g), ctypes.byref(m), None, None, ctypes.byref(o), None,
+                        ctypes.byref(out))
+        assert st == binding.MG_ERR_SHAPE, shape
+        assert level in L.mg_last_error(), L.mg_last_error()
+        assert not out.value
