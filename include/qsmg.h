@@ -236,6 +236,68 @@ mg_status qs_stress_correct(mg_ctx *ctx, const double *v, const double *sigma_st
 mg_status qs_wall_fill(mg_ctx *ctx, double *v, double t);
 
 /* ------------------------------------------------------------------ */
+/* Reverse mode (the paper evaluates no gradient; these entry points      */
+/* differentiate the step of section 3.3 as this library computes it)    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * qs_step_adjoint -- the transpose of one qs_step: the adjoints of the state
+ * a step starts from, given those of the state it produces.  Each equation of
+ * the step is transposed in turn: the stress correction (Eq. 29), the
+ * projection solve (Eq. 30; the scaled operator is symmetric, so its
+ * transpose is one more mg_solve of the same operator with zero walls, to
+ * `tol`), the right-hand side (the corner divergence, transposed to a cell
+ * gradient), the chi update (Eq. 26, z-wall ghosts included), the STZ rate
+ * (Eqs. 20-22; zero derivative at or below yield) and the predictor
+ * (Eq. 27), whose velocity gradient (Eq. 31) is transposed to the corners.
+ * The wall velocities are prescribed, so they carry no adjoint.
+ *   state: device arrays of the state the forward step starts from (v with
+ *       its wall values, sigma, chi), as passed to qs_step; not modified.
+ *   dt: the forward step's dt.
+ *   work_weight: weight w of this step's plastic work 2 D^pl sbar dt h^3
+ *       summed over cells (the growth term of Eq. 26), added to the
+ *       objective.
+ *   vbar (3, nz+1, ny, nx), sigbar (6, nz, ny, nx), chibar (nz, ny, nx):
+ *       device, caller-owned; on entry the adjoints of the step's output
+ *       (v^{n+1}, sigma^{n+1}, chi^{n+1}), on return those of its input.
+ *       Stress adjoints are per stored component (an off-diagonal entry's
+ *       adjoint is the derivative with respect to the stored value, which
+ *       feeds both matrix entries).  vbar's wall planes are ignored on entry
+ *       and zero on return.
+ *   stats: the adjoint solve's statistics (may be NULL).
+ * The first call allocates the adjoint scratch (about 18 doubles a cell) on
+ * the context.  Errors: MG_ERR_ARG, MG_ERR_OOM, MG_ERR_CUDA, MG_ERR_STATE,
+ * and the solve's MG_ERR_NOCONV / MG_ERR_NONFINITE (the outputs are then
+ * those of the last iterate).
+ */
+mg_status qs_step_adjoint(mg_ctx *ctx, const qs_state *state, double dt, double tol,
+                          double work_weight, double *vbar, double *sigbar, double *chibar,
+                          mg_stats *stats);
+
+/*
+ * qs_plastic_work_grad -- W = the plastic work of nsteps qs_steps from
+ * `state` (sum over steps and cells of 2 D^pl sbar dt h^3, D^pl and sbar of
+ * the state each step starts from), and dW/dchi0, the derivative with respect
+ * to the initial chi field.  Runs the steps forward (state is left at the
+ * final state, as after nsteps qs_step calls), keeping a copy of the state
+ * every checkpoint_every steps, then runs qs_step_adjoint backwards one
+ * segment at a time, recomputing the segment's states from its checkpoint
+ * (the forward kernels and reductions are deterministic, so the recomputed
+ * states equal the first ones bit for bit).
+ *   chibar: device (nz, ny, nx), receives dW/dchi0.
+ *   work: host, receives W.
+ *   stats: the last solve's statistics (may be NULL).
+ * Device memory: ceil(nsteps / checkpoint_every) + checkpoint_every state
+ * copies (10 doubles a cell each) plus two adjoint arrays, allocated for the
+ * call and freed before it returns.
+ * Errors: as qs_step and qs_step_adjoint, MG_ERR_ARG for nsteps < 1 or
+ * checkpoint_every < 1.
+ */
+mg_status qs_plastic_work_grad(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
+                               int checkpoint_every, double *chibar, double *work,
+                               mg_stats *stats);
+
+/* ------------------------------------------------------------------ */
 /* Measurement hooks                                                   */
 /* ------------------------------------------------------------------ */
 

@@ -88,6 +88,10 @@ _SIGS = {
     "qs_rhs": (C.c_int, [_P, _P, C.c_double, _P]),
     "qs_stress_correct": (C.c_int, [_P, _P, _P, C.c_double, _P]),
     "qs_wall_fill": (C.c_int, [_P, _P, C.c_double]),
+    "qs_step_adjoint": (C.c_int, [_P, C.POINTER(qs_state), C.c_double, C.c_double, C.c_double,
+                                  _P, _P, _P, C.POINTER(mg_stats)]),
+    "qs_plastic_work_grad": (C.c_int, [_P, C.POINTER(qs_state), C.c_int, C.c_double, C.c_double,
+                                       C.c_int, _P, C.POINTER(C.c_double), C.POINTER(mg_stats)]),
     "mg_profile": (C.c_int, [_P, C.c_int]),
     "mg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_long),
                                   C.POINTER(C.c_long)]),
@@ -211,6 +215,30 @@ class Context:
         if raise_on_error:
             _check(st, "qs_step")
         return st, s
+
+    def step_adjoint(self, state: qs_state, dt, vbar, sigbar, chibar, tol=1e-10, work_weight=1.0,
+                     raise_on_error=True):
+        """qs_step_adjoint: vbar, sigbar, chibar (float64 CUDA tensors) hold the
+        adjoints of the step's output on entry and of its input on return."""
+        s = mg_stats()
+        st = lib().qs_step_adjoint(self.h, C.byref(state), dt, tol, work_weight, _ptr(vbar),
+                                   _ptr(sigbar), _ptr(chibar), C.byref(s))
+        if raise_on_error:
+            _check(st, "qs_step_adjoint")
+        return st, s
+
+    def plastic_work_grad(self, state: qs_state, nsteps, dt, chibar, tol=1e-10,
+                          checkpoint_every=8, raise_on_error=True):
+        """qs_plastic_work_grad: returns (status, W, stats); chibar receives
+        dW/dchi0 and state is advanced by nsteps steps."""
+        s = mg_stats()
+        W = C.c_double()
+        st = lib().qs_plastic_work_grad(self.h, C.byref(state), int(nsteps), dt, tol,
+                                        int(checkpoint_every), _ptr(chibar), C.byref(W),
+                                        C.byref(s))
+        if raise_on_error:
+            _check(st, "qs_plastic_work_grad")
+        return st, W.value, s
 
     def profile(self, enable=True):
         _check(lib().mg_profile(self.h, int(enable)), "mg_profile")

@@ -76,6 +76,8 @@ struct mg_ctx {
     int ncoarse;
     double *partials, *dsum, *hsum;
     double *sig_star, *dpl, *sbar, *chi_tmp, *rhs;
+    // adjoint-step scratch, allocated at the first qs_step_adjoint
+    double *adj_rhs, *adj_lam, *adj_cb, *adj_db, *adj_sbb, *adj_sgb, *adj_Lb;
     // finest-level smoothing timers (event pairs recorded on st)
     bool prof_on, prof_events;
     cudaEvent_t ev[kProfSlots][2];
@@ -1154,6 +1156,160 @@ mg_status qs_wall_fill(mg_ctx *ctx, double *v, double t) {
     }
     CK(wall_fill(wall_params(ctx, t), v, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+// ------------------------------------------------------------ adjoint
+
+mg_status qs_step_adjoint(mg_ctx *ctx, const qs_state *state, double dt, double tol,
+                          double work_weight, double *vbar, double *sigbar, double *chibar,
+                          mg_stats *stats) {
+    CKS(check_ctx(ctx));
+    if (!state || !state->v || !state->sigma || !state->chi || !vbar || !sigbar || !chibar ||
+        !(dt > 0.0)) {
+        set_err("qs_step_adjoint: null array or dt <= 0");
+        return MG_ERR_ARG;
+    }
+    if (!ctx->has_stz) {
+        set_err("qs_step_adjoint: context was set up without stz parameters");
+        return MG_ERR_ARG;
+    }
+    const Dims &d = ctx->L[0];
+    const size_t nc = (size_t)d.nx * d.ny * d.nz, nv = corner_count(d);
+    if (!ctx->adj_rhs) {
+        CKS(dalloc(ctx, &ctx->adj_rhs, nv));
+        CKS(dalloc(ctx, &ctx->adj_lam, nv));
+        CKS(dalloc(ctx, &ctx->adj_cb, nc));
+        CKS(dalloc(ctx, &ctx->adj_db, nc));
+        CKS(dalloc(ctx, &ctx->adj_sbb, nc));
+        CKS(dalloc(ctx, &ctx->adj_sgb, 6 * nc));
+        CKS(dalloc(ctx, &ctx->adj_Lb, 9 * nc));
+    }
+    const StepParams p = step_params(ctx, dt);
+    // the forward D^pl and sbar of this state
+    CK(stress_predict(p, state->v, state->sigma, state->chi, ctx->sig_star, ctx->dpl, ctx->sbar,
+                      ctx->st));
+    // stress correction (Eq. 29), then the projection solve (its own transpose)
+    CK(adj_correct(p, sigbar, vbar, ctx->adj_rhs, ctx->st));
+    CK(cudaMemsetAsync(ctx->adj_lam, 0, nv * sizeof(double), ctx->st));
+    const mg_status s = mg_solve(ctx, ctx->adj_rhs, ctx->adj_lam, tol, stats);
+    if (s != MG_OK && s != MG_ERR_NOCONV) return s;
+    // chi update (Eq. 26), predictor and right-hand side (Eq. 27, Eq. 30),
+    // velocity gradient (Eq. 31)
+    CK(adj_chi(p, state->sigma, state->chi, ctx->dpl, ctx->sbar, chibar, ctx->adj_cb,
+               ctx->adj_db, ctx->adj_sbb, ctx->adj_sgb, ctx->st));
+    CK(adj_predict(p, state->v, ctx->adj_lam, state->sigma, state->chi, sigbar, ctx->adj_cb,
+                   ctx->adj_db, ctx->adj_sbb, ctx->adj_sgb, chibar, ctx->adj_Lb, work_weight,
+                   ctx->st));
+    CK(adj_grad_transpose(p, ctx->adj_Lb, vbar, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return s;
+}
+
+namespace {
+
+// device copies of a state, freed when the holder goes out of scope
+struct StateStore {
+    std::vector<double *> bufs;
+    ~StateStore() {
+        for (double *b : bufs) cudaFree(b);
+    }
+    double *get(size_t n) {
+        void *q = nullptr;
+        if (cudaMalloc(&q, n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        bufs.push_back((double *)q);
+        return (double *)q;
+    }
+};
+
+}  // namespace
+
+mg_status qs_plastic_work_grad(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
+                               int checkpoint_every, double *chibar, double *work,
+                               mg_stats *stats) {
+    CKS(check_ctx(ctx));
+    if (!state || !state->v || !state->sigma || !state->chi || !chibar || !work ||
+        nsteps < 1 || checkpoint_every < 1 || !(dt > 0.0)) {
+        set_err("qs_plastic_work_grad: null array, nsteps < 1, checkpoint_every < 1 or dt <= 0");
+        return MG_ERR_ARG;
+    }
+    if (!ctx->has_stz || !ctx->has_bc) {
+        set_err("qs_plastic_work_grad: context was set up without stz/bc parameters");
+        return MG_ERR_ARG;
+    }
+    const Dims &d = ctx->L[0];
+    const size_t nc = (size_t)d.nx * d.ny * d.nz, nv = corner_count(d);
+    const int seg = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+    const int ncp = (nsteps + seg - 1) / seg;
+    StateStore store;
+    // checkpoints (every seg steps) and the states of one segment
+    std::vector<qs_state> cp(ncp), ss(seg);
+    for (int c = 0; c < ncp + seg; c++) {
+        qs_state &q = c < ncp ? cp[c] : ss[c - ncp];
+        q.v = store.get(nv);
+        q.sigma = store.get(6 * nc);
+        q.chi = store.get(nc);
+        if (!q.v || !q.sigma || !q.chi) {
+            set_err("qs_plastic_work_grad: out of device memory for %d checkpoints", ncp + seg);
+            return MG_ERR_OOM;
+        }
+    }
+    double *vbar = store.get(nv), *sigbar = store.get(6 * nc);
+    if (!vbar || !sigbar) {
+        set_err("qs_plastic_work_grad: out of device memory");
+        return MG_ERR_OOM;
+    }
+    auto copy_state = [&](const qs_state &from, qs_state &to) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(to.v, from.v, nv * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, ctx->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(to.sigma, from.sigma, 6 * nc * sizeof(double),
+                                cudaMemcpyDeviceToDevice, ctx->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(to.chi, from.chi, nc * sizeof(double), cudaMemcpyDeviceToDevice,
+                                ctx->st);
+        to.t = from.t;
+        to.step = from.step;
+        return e;
+    };
+    // forward, keeping checkpoints and summing the plastic work of each step
+    // (D^pl and sbar of the state the step starts from)
+    const double wscale = 2.0 * dt * ctx->h * ctx->h * ctx->h;
+    double W = 0.0;
+    for (int n = 0; n < nsteps; n++) {
+        if (n % seg == 0) CK(copy_state(*state, cp[n / seg]));
+        const mg_status s = qs_step(ctx, state, dt, tol, stats);
+        if (s != MG_OK) return s;
+        CK(dot_cells(ctx->dpl, ctx->sbar, (long)nc, ctx->partials, ctx->st));
+        CK(sum_partials(ctx->partials, ctx->dsum, ctx->st));
+        CK(cudaMemcpyAsync(ctx->hsum, ctx->dsum, sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        W += wscale * ctx->hsum[0];
+    }
+    // reverse, one segment at a time from its checkpoint
+    CK(cudaMemsetAsync(vbar, 0, nv * sizeof(double), ctx->st));
+    CK(cudaMemsetAsync(sigbar, 0, 6 * nc * sizeof(double), ctx->st));
+    CK(cudaMemsetAsync(chibar, 0, nc * sizeof(double), ctx->st));
+    for (int c = ncp - 1; c >= 0; c--) {
+        const int n0 = c * seg, n1 = n0 + seg < nsteps ? n0 + seg : nsteps;
+        CK(copy_state(cp[c], ss[0]));
+        for (int n = n0; n + 1 < n1; n++) {
+            CK(copy_state(ss[n - n0], ss[n - n0 + 1]));
+            const mg_status s = qs_step(ctx, &ss[n - n0 + 1], dt, tol, nullptr);
+            if (s != MG_OK) return s;
+        }
+        for (int n = n1 - 1; n >= n0; n--) {
+            const mg_status s = qs_step_adjoint(ctx, &ss[n - n0], dt, tol, 1.0, vbar, sigbar,
+                                                chibar, stats);
+            if (s != MG_OK) return s;
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    *work = W;
     return MG_OK;
 }
 

@@ -159,4 +159,27 @@ cudaError_t stress_correct(const StepParams &p, const double *v, const double *s
                            double *sig, const double *chi_src, double *chi_dst, cudaStream_t s);
 cudaError_t wall_fill(const WallParams &w, double *v, cudaStream_t s);
 
+// ---------------------------------------------------------------- adjoint
+// (transposes of the step's equations; stored stress adjoints, see
+// step_kernels.cu)
+// rhs_out (interior corners) = vb1 - dt G^T (C : sigbar1); walls zero
+cudaError_t adj_correct(const StepParams &p, const double *sb1, const double *vb1,
+                        double *rhs_out, cudaStream_t s);
+// transpose of the chi update: chib, Db, sbb per cell, sgb 6 per cell
+cudaError_t adj_chi(const StepParams &p, const double *sig, const double *chi, const double *dpl,
+                    const double *sbar, const double *cb1, double *chib, double *Db, double *sbb,
+                    double *sgb, cudaStream_t s);
+// transpose of the predictor and right-hand side: sb1 in, sigma^n adjoint
+// out (in place); chib_out; Lb = velocity-gradient adjoint, 9 per cell
+cudaError_t adj_predict(const StepParams &p, const double *v, const double *lam,
+                        const double *sig, const double *chi, double *sb1, const double *chib,
+                        const double *Db, const double *sbb, const double *sgb, double *chib_out,
+                        double *Lb, double w_work, cudaStream_t s);
+// vb (interior corners) = G^T Lb; walls zero
+cudaError_t adj_grad_transpose(const StepParams &p, const double *Lb, double *vb,
+                               cudaStream_t s);
+// sum over n cells of a * b into partials[kRedBlocks]
+cudaError_t dot_cells(const double *a, const double *b, long n, double *partials,
+                      cudaStream_t s);
+
 }  // namespace qsmg

@@ -365,3 +365,428 @@ cudaError_t wall_fill(const WallParams &w, double *v, cudaStream_t s) {
 }
 
 }  // namespace qsmg
+
+// ------------------------------------------------------------------ adjoint
+//
+// Reverse of one projection step for the gradient of an objective through
+// the step: given the adjoints (vbar, sigbar, chibar) of the state after the
+// step, the adjoints of the state before it.  Each kernel is the transpose
+// of one forward equation (Eqs. 26, 27, 29, 31 and the right-hand side of
+// Eq. 30); the projection solve is its own transpose (the scaled operator is
+// symmetric) and runs through the multigrid solver.  Stored stress adjoints
+// follow the stored components: for an off-diagonal component the adjoint is
+// the sum of the two full-matrix entries, so the full-matrix adjoint is half
+// of it.
+
+namespace qsmg {
+namespace {
+
+// STZ rate (as stz_rate) with its partial derivatives in sbar and chi
+__device__ __forceinline__ void stz_rate_d(const StzConst &c, double sbar, double inv_sbar,
+                                           double chi, double &D, double &Ds, double &Dc) {
+    if (!(sbar > c.sY) || !(chi > 0.0)) {
+        D = Ds = Dc = 0.0;
+        return;
+    }
+    const double y = -c.ez_K / chi, x = c.beta * sbar;
+    const double ep = exp(x + y), em = exp(y - x);
+    const double f = 1.0 - c.sY * inv_sbar;
+    D = (ep + em) * c.half_eDT_over_tau0 * f;
+    Ds = c.half_eDT_over_tau0 * (c.beta * (ep - em) * f + (ep + em) * c.sY * inv_sbar * inv_sbar);
+    Dc = D * c.ez_K / (chi * chi);
+}
+
+// deviatoric part and sbar of a stored stress
+__device__ __forceinline__ void dev_of(const double s[6], double S0[3][3], double &sb,
+                                       double &inv_sb) {
+    const double m = (s[0] + s[1] + s[2]) * (1.0 / 3.0);
+    S0[0][0] = s[0] - m;
+    S0[1][1] = s[1] - m;
+    S0[2][2] = s[2] - m;
+    S0[1][2] = S0[2][1] = s[3];
+    S0[0][2] = S0[2][0] = s[4];
+    S0[0][1] = S0[1][0] = s[5];
+    sb = sbar_of(s);
+    inv_sb = sb > 0.0 ? 1.0 / sb : 0.0;
+}
+
+// stored adjoint of a symmetric full-matrix adjoint X (added, times w)
+__device__ __forceinline__ void add_stored(double out[6], const double X[3][3], double w) {
+    out[0] += w * X[0][0];
+    out[1] += w * X[1][1];
+    out[2] += w * X[2][2];
+    out[3] += w * (X[1][2] + X[2][1]);
+    out[4] += w * (X[0][2] + X[2][0]);
+    out[5] += w * (X[0][1] + X[1][0]);
+}
+
+// Transpose of the chi diffusion at one z-wall ghost face.  Cell P (boundary
+// layer) has a ghost neighbour with chi_g = 2 chi_P - chi_Q and sigma_g =
+// 2 sigma_P - sigma_Q (Q the next layer inward); its face term in P's update
+// is a (D_P + D_g)/2 (chi_g - chi_P), a = chibar'_P dt l^2 / (c0 h^2).
+// Returns the adjoint contributions: to chi_P (cP), chi_Q (cQ), D_P (dP) and
+// the full-matrix stress adjoint Sg of the ghost (P receives 2 Sg, Q -Sg).
+struct GhostAdj {
+    double cP, cQ, dP;
+    double Sg[3][3];
+};
+__device__ __forceinline__ GhostAdj ghost_adj(const StzConst &c, const double *__restrict__ sig,
+                                              const double *__restrict__ chi,
+                                              const double *__restrict__ dpl, long nc, long qP,
+                                              long qQ, double a) {
+    GhostAdj G;
+    double sg[6];
+#pragma unroll
+    for (int n = 0; n < 6; n++) sg[n] = 2.0 * sig[n * nc + qP] - sig[n * nc + qQ];
+    const double cP = chi[qP], cg = 2.0 * cP - chi[qQ], DP = dpl[qP];
+    double S0[3][3], sb, inv;
+    dev_of(sg, S0, sb, inv);
+    double Dg, Dgs, Dgc;
+    stz_rate_d(c, sb, inv, cg, Dg, Dgs, Dgc);
+    const double half_gap = 0.5 * (cg - cP);
+    // d/dchi_g = a (D_P + D_g)/2 + a (chi_g - chi_P)/2 dD_g/dchi_g; chi_g = 2 chi_P - chi_Q
+    const double dg = a * 0.5 * (DP + Dg) + a * half_gap * Dgc;
+    G.cP = -a * 0.5 * (DP + Dg) + 2.0 * dg;
+    G.cQ = -dg;
+    G.dP = a * half_gap;
+    const double w = a * half_gap * Dgs * 0.5 * inv;  // Dbar_g dD_g/dsbar_g / (2 sbar_g)
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s = 0; s < 3; s++) G.Sg[r][s] = w * S0[r][s];
+    return G;
+}
+
+// Transpose of Eq. (26) in gather form, per cell P: chib (adjoint of chi^n
+// through the chi update), Db and sbb (adjoints of D^pl_P and sbar_P), and
+// sgb (stress adjoint from the z-wall ghosts, stored; zero away from the two
+// outer layers on each side)
+__global__ void k_adj_chi(StepParams p, StzConst c, const double *__restrict__ sig,
+                          const double *__restrict__ chi, const double *__restrict__ dpl,
+                          const double *__restrict__ sbar, const double *__restrict__ cb1,
+                          double *__restrict__ chib, double *__restrict__ Db,
+                          double *__restrict__ sbb, double *__restrict__ sgb, long nc) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    int i, j, k;
+    if (!cell_ijk(nx, ny, i, j, k)) return;
+    const long pl = (long)nx * ny;
+    const long q = (long)k * pl + (long)j * nx + i;
+    const double kap = p.dt / p.c0, kd = kap * (p.l * p.l) / (p.h * p.h);
+    const double bP = cb1[q], cP = chi[q], DP = dpl[q], sP = sbar[q];
+    double cb = bP - bP * kap * 2.0 * DP * sP / p.sY;
+    double db = bP * kap * 2.0 * sP / p.sY * (p.chi_inf - cP);
+    const double sbv = bP * kap * 2.0 * DP / p.sY * (p.chi_inf - cP);
+    const int ip = (i + 1 < nx) ? i + 1 : 0, im = i ? i - 1 : nx - 1;
+    const int jp = (j + 1 < ny) ? j + 1 : 0, jm = j ? j - 1 : ny - 1;
+    long nb[6];
+    int nn = 0;
+    nb[nn++] = (long)k * pl + (long)j * nx + ip;
+    nb[nn++] = (long)k * pl + (long)j * nx + im;
+    nb[nn++] = (long)k * pl + (long)jp * nx + i;
+    nb[nn++] = (long)k * pl + (long)jm * nx + i;
+    if (k + 1 < nz) nb[nn++] = q + pl;
+    if (k > 0) nb[nn++] = q - pl;
+    for (int n = 0; n < nn; n++) {
+        const double bN = cb1[nb[n]], DN = dpl[nb[n]], cN = chi[nb[n]];
+        cb += kd * 0.5 * (DP + DN) * (bN - bP);
+        db += kd * 0.5 * (cN - cP) * (bP - bN);
+    }
+    double sg[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // this cell's own ghost faces
+    if (k == nz - 1) {
+        const GhostAdj G = ghost_adj(c, sig, chi, dpl, nc, q, q - pl, bP * kd);
+        cb += G.cP;
+        db += G.dP;
+        add_stored(sg, G.Sg, 2.0);
+    }
+    if (k == 0) {
+        const GhostAdj G = ghost_adj(c, sig, chi, dpl, nc, q, q + pl, bP * kd);
+        cb += G.cP;
+        db += G.dP;
+        add_stored(sg, G.Sg, 2.0);
+    }
+    // this cell as the inner layer of a neighbour's ghost
+    if (k == nz - 2) {
+        const GhostAdj G = ghost_adj(c, sig, chi, dpl, nc, q + pl, q, cb1[q + pl] * kd);
+        cb += G.cQ;
+        add_stored(sg, G.Sg, -1.0);
+    }
+    if (k == 1) {
+        const GhostAdj G = ghost_adj(c, sig, chi, dpl, nc, q - pl, q, cb1[q - pl] * kd);
+        cb += G.cQ;
+        add_stored(sg, G.Sg, -1.0);
+    }
+    chib[q] = cb;
+    Db[q] = db;
+    sbb[q] = sbv;
+#pragma unroll
+    for (int n = 0; n < 6; n++) sgb[n * nc + q] = sg[n];
+}
+
+// Transpose of Eq. (27) (with the work term and the right-hand side of
+// Eq. 30 folded in), per cell: from the stored adjoint of sigma^{n+1}
+// (sb1, which is also that of sigma*), the gradient of the adjoint solve
+// (lam), and the chi-update adjoints, the adjoints of sigma^n (written over
+// sb1), chi^n (chib_out) and of the velocity gradient L (Lb, 9 per cell,
+// row-major).  w_work weighs the step's plastic work 2 D^pl sbar dt h^3.
+__global__ void k_adj_predict(StepParams p, StzConst c, const double *__restrict__ v,
+                              const double *__restrict__ lam, const double *__restrict__ sig,
+                              const double *__restrict__ chi, double *__restrict__ sb1,
+                              const double *__restrict__ chib, const double *__restrict__ Db_in,
+                              const double *__restrict__ sbb_in, const double *__restrict__ sgb,
+                              double *__restrict__ chib_out, double *__restrict__ Lb,
+                              double w_work, long nc) {
+    CellColumn C;
+    if (!cell_column(p.nx, p.ny, p.nz, C)) return;
+    const double inv4h = 0.25 / p.h, dt = p.dt, mu = p.mu;
+    const double rhs_scale = p.h * p.h / (p.mu * dt);  // (h^2/(mu dt)) / (4h) * 4h
+    const double work = w_work * 2.0 * dt * p.h * p.h * p.h;
+    GradPlane vlo = grad_plane(v, C.cs, C.k0 * C.pl, C.r0, C.r1, C.i, C.i1);
+    GradPlane llo = grad_plane(lam, C.cs, C.k0 * C.pl, C.r0, C.r1, C.i, C.i1);
+    for (int k = C.k0; k < C.k1; k++) {
+        const GradPlane vhi = grad_plane(v, C.cs, (k + 1) * C.pl, C.r0, C.r1, C.i, C.i1);
+        const GradPlane lhi = grad_plane(lam, C.cs, (k + 1) * C.pl, C.r0, C.r1, C.i, C.i1);
+        const long q = k * C.pl + C.r0 + C.i;
+        double L[3][3], Gl[3][3];
+        grad_cell(vlo, vhi, inv4h, L);
+        grad_cell(llo, lhi, inv4h, Gl);
+        vlo = vhi;
+        llo = lhi;
+        double s6[6], ss[6];
+#pragma unroll
+        for (int n = 0; n < 6; n++) {
+            s6[n] = sig[n * nc + q];
+            ss[n] = sb1[n * nc + q];
+        }
+        // right-hand side b = (h^2/(mu dt)) corner-div sigma*: its transpose
+        // is -(h^2/(mu dt)) times the cell gradient of the solve's adjoint
+        ss[0] -= rhs_scale * Gl[0][0];
+        ss[1] -= rhs_scale * Gl[1][1];
+        ss[2] -= rhs_scale * Gl[2][2];
+        ss[3] -= rhs_scale * (Gl[1][2] + Gl[2][1]);
+        ss[4] -= rhs_scale * (Gl[0][2] + Gl[2][0]);
+        ss[5] -= rhs_scale * (Gl[0][1] + Gl[1][0]);
+        // full-matrix adjoint of sigma*
+        const double B[3][3] = {{ss[0], 0.5 * ss[5], 0.5 * ss[4]},
+                                {0.5 * ss[5], ss[1], 0.5 * ss[3]},
+                                {0.5 * ss[4], 0.5 * ss[3], ss[2]}};
+        const double S[3][3] = {{s6[0], s6[5], s6[4]}, {s6[5], s6[1], s6[3]}, {s6[4], s6[3], s6[2]}};
+        double S0[3][3], sb, inv;
+        dev_of(s6, S0, sb, inv);
+        double D, Ds, Dc;
+        stz_rate_d(c, sb, inv, chi[q], D, Ds, Dc);
+        double db = Db_in[q] + work * sb;
+        double sbv = sbb_in[q] + work * D;
+        const double trL = L[0][0] + L[1][1] + L[2][2];
+        const double P = 2.0 * mu * dt * D * inv;
+        const double trB = (B[0][0] + B[1][1] + B[2][2]) * (1.0 / 3.0);
+        double Sb[3][3], Lbar[3][3];
+        double BdotS = 0.0, BdotS0 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                BdotS += B[a][b] * S[a][b];
+                BdotS0 += B[a][b] * S0[a][b];
+            }
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                double ltb = 0.0, bl = 0.0, bs = 0.0;
+#pragma unroll
+                for (int e = 0; e < 3; e++) {
+                    ltb += L[e][a] * B[e][b];
+                    bl += B[a][e] * L[e][b];
+                    bs += B[a][e] * S[e][b];
+                }
+                Sb[a][b] = B[a][b] + dt * (ltb + bl - trL * B[a][b]) -
+                           P * (B[a][b] - (a == b ? trB : 0.0));
+                Lbar[a][b] = dt * (2.0 * bs - (a == b ? BdotS : 0.0));
+            }
+        const double Pb = -BdotS0;
+        db += Pb * 2.0 * mu * dt * inv;
+        sbv -= Pb * 2.0 * mu * dt * D * inv * inv;
+        sbv += db * Ds;
+        chib_out[q] = chib[q] + db * Dc;
+        double out[6];
+#pragma unroll
+        for (int n = 0; n < 6; n++) out[n] = sgb[n * nc + q];
+        const double w = sbv * 0.5 * inv;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) Sb[a][b] += w * S0[a][b];
+        add_stored(out, Sb, 1.0);
+#pragma unroll
+        for (int n = 0; n < 6; n++) sb1[n * nc + q] = out[n];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) Lb[(a * 3 + b) * nc + q] = Lbar[a][b];
+    }
+}
+
+// cell tensors read as full 3 x 3 matrices: the stored adjoint of
+// sigma^{n+1} mapped through C (C:Sigmabar, symmetric), or a general one
+// stored row-major in 9 arrays
+struct LoadCSym {
+    const double *sb;
+    long nc;
+    double lam, mu;
+    __device__ __forceinline__ void operator()(long q, double T[3][3]) const {
+        const double s0 = sb[q], s1 = sb[nc + q], s2 = sb[2 * nc + q];
+        const double tr = s0 + s1 + s2;
+        T[0][0] = lam * tr + 2.0 * mu * s0;
+        T[1][1] = lam * tr + 2.0 * mu * s1;
+        T[2][2] = lam * tr + 2.0 * mu * s2;
+        T[1][2] = T[2][1] = mu * sb[3 * nc + q];
+        T[0][2] = T[2][0] = mu * sb[4 * nc + q];
+        T[0][1] = T[1][0] = mu * sb[5 * nc + q];
+    }
+};
+struct LoadFull {
+    const double *t;
+    long nc;
+    __device__ __forceinline__ void operator()(long q, double T[3][3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) T[a][b] = t[(a * 3 + b) * nc + q];
+    }
+};
+
+// the corner divergence of k_div_rhs for a general cell tensor T (row a =
+// output component): the 4 cells (jm..j, im..i) of one cell layer
+template <class Load>
+__device__ __forceinline__ DivLayer tensor_layer(const Load &ld, long base, long rj0, long rj1,
+                                                 int im, int i) {
+    double T00[3][3], T01[3][3], T10[3][3], T11[3][3];
+    ld(base + rj0 + im, T00);
+    ld(base + rj0 + i, T01);
+    ld(base + rj1 + im, T10);
+    ld(base + rj1 + i, T11);
+    DivLayer L;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        L.X[a] = (T01[a][0] - T00[a][0]) + (T11[a][0] - T10[a][0]);
+        L.Y[a] = (T10[a][1] - T00[a][1]) + (T11[a][1] - T01[a][1]);
+        L.Z[a] = (T00[a][2] + T01[a][2]) + (T10[a][2] + T11[a][2]);
+    }
+    return L;
+}
+
+// out = add + scale * corner-div T at the interior corners (wall planes of
+// out are left alone); the transpose of the cell gradient of Eq. (31) is
+// -1/(4h) times this divergence
+template <class Load>
+__global__ void k_corner_div(StepParams p, Load ld, const double *__restrict__ add,
+                             double *__restrict__ out, double scale) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const int k0 = 1 + blockIdx.z * kDivChunk;
+    const int k1 = k0 + kDivChunk < nz ? k0 + kDivChunk : nz;
+    const int im = i ? i - 1 : nx - 1, jm = j ? j - 1 : ny - 1;
+    const long pl = (long)nx * ny, cs = (long)(nz + 1) * pl;
+    const long rj0 = (long)jm * nx, rj1 = (long)j * nx;
+    DivLayer lo = tensor_layer(ld, (long)(k0 - 1) * pl, rj0, rj1, im, i);
+    for (int k = k0; k < k1; k++) {
+        const DivLayer hi = tensor_layer(ld, (long)k * pl, rj0, rj1, im, i);
+        const long node = (long)k * pl + (long)j * nx + i;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double d = (lo.X[a] + hi.X[a]) + (lo.Y[a] + hi.Y[a]) + (hi.Z[a] - lo.Z[a]);
+            out[a * cs + node] = (add ? add[a * cs + node] : 0.0) + scale * d;
+        }
+        lo = hi;
+    }
+}
+
+// sum over cells of a * b into partials[kRedBlocks] (fixed geometry, so the
+// total is bitwise reproducible)
+__global__ void __launch_bounds__(kRedThreads)
+    k_dot_cells(const double *__restrict__ a, const double *__restrict__ b, long n,
+                double *__restrict__ partials) {
+    __shared__ double red[kRedThreads / 32];
+    double acc = 0.0;
+    for (long t = (long)blockIdx.x * kRedThreads + threadIdx.x; t < n;
+         t += (long)gridDim.x * kRedThreads)
+        acc += a[t] * b[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kRedThreads / 32; w++) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+cudaError_t zero_walls(const StepParams &p, double *x, cudaStream_t s) {
+    const long pl = (long)p.nx * p.ny, cs = (long)(p.nz + 1) * pl;
+    for (int a = 0; a < 3; a++) {
+        cudaError_t e = cudaMemsetAsync(x + a * cs, 0, pl * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(x + a * cs + (long)p.nz * pl, 0, pl * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t adj_correct(const StepParams &p, const double *sb1, const double *vb1,
+                        double *rhs_out, cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    cudaError_t e = zero_walls(p, rhs_out, s);
+    if (e != cudaSuccess) return e;
+    const LoadCSym ld{sb1, nc, p.lam, p.mu};
+    k_corner_div<LoadCSym><<<cell_grid(p.nx, p.ny, (p.nz - 1 + kDivChunk - 1) / kDivChunk),
+                             kBlock, 0, s>>>(p, ld, vb1, rhs_out, -p.dt * 0.25 / p.h);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t adj_chi(const StepParams &p, const double *sig, const double *chi, const double *dpl,
+                    const double *sbar, const double *cb1, double *chib, double *Db, double *sbb,
+                    double *sgb, cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    k_adj_chi<<<cell_grid(p.nx, p.ny, p.nz), kBlock, 0, s>>>(p, stz_const(p), sig, chi, dpl, sbar,
+                                                              cb1, chib, Db, sbb, sgb, nc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t adj_predict(const StepParams &p, const double *v, const double *lam,
+                        const double *sig, const double *chi, double *sb1, const double *chib,
+                        const double *Db, const double *sbb, const double *sgb, double *chib_out,
+                        double *Lb, double w_work, cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    k_adj_predict<<<cell_grid(p.nx, p.ny, (p.nz + kCellChunk - 1) / kCellChunk), kBlock, 0, s>>>(
+        p, stz_const(p), v, lam, sig, chi, sb1, chib, Db, sbb, sgb, chib_out, Lb, w_work, nc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t adj_grad_transpose(const StepParams &p, const double *Lb, double *vb,
+                               cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    cudaError_t e = zero_walls(p, vb, s);
+    if (e != cudaSuccess) return e;
+    const LoadFull ld{Lb, nc};
+    k_corner_div<LoadFull><<<cell_grid(p.nx, p.ny, (p.nz - 1 + kDivChunk - 1) / kDivChunk),
+                             kBlock, 0, s>>>(p, ld, nullptr, vb, -0.25 / p.h);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t dot_cells(const double *a, const double *b, long n, double *partials,
+                      cudaStream_t s) {
+    k_dot_cells<<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, partials);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace qsmg
