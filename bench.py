@@ -190,8 +190,11 @@ def config(w, extra=None):
     c = {"workload": "simple shear %dx%dx%d cells, STZ-active (sigma_xz0 = %.1f GPa), chi0 seeded "
                      "Gaussian field 600 K / 30 K / l_c = 4 cells, dt = 200 t_s, warm-started "
                      "solves to rel. resid 1e-10" % (w.nx, w.ny, w.nz, PRELOAD / 1e9),
-         "grid": [w.nx, w.ny, w.nz], "unknowns": 3 * w.nx * w.ny * (w.nz - 1),
-         "l2": "inputs larger than L2 (state 1.3 GB, hierarchy 2+ GB)"}
+         "grid": [w.nx, w.ny, w.nz], "unknowns": 3 * w.nx * w.ny * (w.nz - 1)}
+    # v (corners) + sigma and chi (cells), FP64; L2 is 129 MB
+    state_gb = 8.0 * (3 * (w.nz + 1) + 7 * w.nz) * w.nx * w.ny / 1e9
+    c["l2"] = ("inputs larger than L2 (state %.2f GB, plus the multigrid hierarchy)" % state_gb
+               if state_gb > 0.129 else "inputs smaller than L2 (state %.3f GB)" % state_gb)
     if extra:
         c.update(extra)
     return c
