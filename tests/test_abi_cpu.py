@@ -56,3 +56,12 @@ def test_setup_rejects_a_coarsest_level_beyond_the_dense_solve():
         assert st == binding.MG_ERR_SHAPE, shape
         assert level in L.mg_last_error(), L.mg_last_error()
         assert not out.value
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the built CUDA library the binding raises."""
+    import pytest
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "lib_path", lambda: "/nonexistent/libqsmg.so")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        binding.lib()
