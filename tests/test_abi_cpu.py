@@ -65,3 +65,13 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(binding, "lib_path", lambda: "/nonexistent/libqsmg.so")
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         binding.lib()
+
+
+def test_reverse_mode_entry_points_reject_null_arguments_without_gpu():
+    L = binding.lib()
+    assert L.qs_step_adjoint(None, None, 1.0, 1e-10, 1.0, None, None, None,
+                             None) == binding.MG_ERR_ARG
+    W = ctypes.c_double()
+    assert L.qs_plastic_work_grad(None, None, 4, 1.0, 1e-10, 2, None, ctypes.byref(W),
+                                  None) == binding.MG_ERR_ARG
+    assert b"null" in L.mg_last_error()
