@@ -5,4 +5,4 @@ CUDA library built by ``build``; ``inputs`` draws the seeded synthetic fields.
 """
 from . import build, inputs  # noqa: F401
 from .binding import (MG_FP64, MG_MIXED, Context, QSMGError, lib, make_state,  # noqa: F401
-                      mg_stats, qs_state)
+                      mg_stats, plastic_work, qs_state)

@@ -299,6 +299,50 @@ class Context:
         _check(lib().qs_wall_fill(self.h, _ptr(v), t), "qs_wall_fill")
 
 
+def plastic_work(ctx: "Context", v0, sigma0, chi0, t0, nsteps, dt, tol=1e-10, checkpoint_every=8):
+    """The plastic work W of nsteps projection steps from (v0, sigma0, chi0)
+    at time t0, differentiable with respect to chi0 (a torch.autograd.Function
+    over qs_plastic_work_grad; the inputs are copied, not advanced)."""
+    return _PlasticWork.apply(chi0, ctx, v0, sigma0, t0, nsteps, dt, tol, checkpoint_every)
+
+
+def _plastic_work_class():
+    import torch
+
+    class PlasticWork(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, chi0, ctx, v0, sigma0, t0, nsteps, dt, tol, checkpoint_every):
+            v = v0.detach().clone()
+            sig = sigma0.detach().clone()
+            chi = chi0.detach().clone()
+            state = make_state(v, sig, chi, t0)
+            grad = torch.zeros_like(chi)
+            _, W, _ = ctx.plastic_work_grad(state, nsteps, dt, grad, tol=tol,
+                                            checkpoint_every=checkpoint_every)
+            fctx.save_for_backward(grad)
+            return torch.tensor(W, dtype=torch.float64, device=chi0.device)
+
+        @staticmethod
+        def backward(fctx, gW):
+            (grad,) = fctx.saved_tensors
+            return (gW * grad,) + (None,) * 8
+
+    return PlasticWork
+
+
+class _Lazy:
+    def __init__(self, make):
+        self._make, self._cls = make, None
+
+    def apply(self, *args):
+        if self._cls is None:
+            self._cls = self._make()
+        return self._cls.apply(*args)
+
+
+_PlasticWork = _Lazy(_plastic_work_class)
+
+
 def launch_count() -> int:
     """Kernels the library has launched since it was loaded."""
     return lib().mg_launch_count()

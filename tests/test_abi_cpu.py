@@ -75,3 +75,11 @@ def test_reverse_mode_entry_points_reject_null_arguments_without_gpu():
     assert L.qs_plastic_work_grad(None, None, 4, 1.0, 1e-10, 2, None, ctypes.byref(W),
                                   None) == binding.MG_ERR_ARG
     assert b"null" in L.mg_last_error()
+
+
+def test_plastic_work_is_an_autograd_function_over_the_c_entry_point():
+    import torch
+    cls = binding._plastic_work_class()
+    assert issubclass(cls, torch.autograd.Function)
+    from paper_1904_03808_gb300 import plastic_work
+    assert plastic_work is binding.plastic_work
