@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--inner", type=int, default=INNER)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-only", action="store_true")
+    ap.add_argument("--two-phase", action="store_true",
+                    help="--sweep-only: the two-launch finest sweep instead of the fused one")
     ap.add_argument("--disc", action="store_true")
     ap.add_argument("--dt-ts", type=float, default=2.0e4)
     ap.add_argument("--kind", type=int, default=1, choices=[1, 2, 3],
@@ -67,6 +69,18 @@ def parse():
     ap.add_argument("--chi", default="450,15,5",
                     help="disc chi0 recipe: mean K, std K, correlation length in cells")
     ap.add_argument("--nz", type=int, default=0)
+    ap.add_argument("--c3-steps", type=int, default=50,
+                    help="steps of the mixed-vs-FP64 lockstep run from the initial state")
+    ap.add_argument("--c2", action="store_true",
+                    help="128^3 x 100 FP64 steps on the GPU in lockstep with the CPU oracle")
+    ap.add_argument("--preload", type=float, default=None,
+                    help="--c2: initial sigma_xz in Pa (0: the literal unstressed start)")
+    ap.add_argument("--cpu-report", action="store_true",
+                    help="the CPU oracle's complete runs: 32^3 solve, 256^3 cold solve and "
+                         "first 5 steps, 512^3 first step")
+    ap.add_argument("--grad", action="store_true",
+                    help="64^3 x 40 FP64 steps: plastic work forward alone and with dW/dchi0")
+    ap.add_argument("--every", type=int, default=8, help="--grad: checkpoint interval")
     return ap.parse_args()
 
 
@@ -156,8 +170,9 @@ def run_sweeps(args):
     nz = args.nz or n
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
+    from paper_1904_03808_gb300.binding import MG_FLAG_TWO_PHASE
     ctx = Context(n, n, nz, 2.0e-2 / n, I.TABLE1["K"], I.TABLE1["mu"], precision=MG_MIXED,
-                  stream=stream)
+                  stream=stream, flags=MG_FLAG_TWO_PHASE if args.two_phase else 0)
     g = torch.Generator(device=dev).manual_seed(5)
     x = torch.rand((3, nz + 1, n, n), device=dev, dtype=torch.float32, generator=g) - 0.5
     b = torch.rand((3, nz + 1, n, n), device=dev, dtype=torch.float32, generator=g) - 0.5
@@ -175,7 +190,8 @@ def run_sweeps(args):
     ctx.close()
     t = sm_ms / max(sweeps, 1)
     nodes = n * n * (nz - 1)
-    return {"mode": "sweep-only", "grid": [n, n, nz], "sweeps": sweeps, "sweep_ms": t,
+    return {"mode": "sweep-only", "kernel": "two-phase" if args.two_phase else "default",
+            "grid": [n, n, nz], "sweeps": sweeps, "sweep_ms": t,
             "achieved_gbs": SMOOTH_BYTES * nodes / (t / 1e3) / 1e9,
             "launches_per_sweep": launches / max(sweeps, 1), "clocks": clk}
 
@@ -312,32 +328,95 @@ def traffic_per_sweep(n_nodes):
 
 # --------------------------------------------------------------------- oracle
 
-def oracle_sample(w, v, sig, chi, t, cycles_per_solve):
-    """Time the FP64 CPU oracle on a bounded sample of the same workload:
-    the pointwise step pieces at full size, one V-cycle and one residual norm;
-    per-solve seconds = pointwise + cycles_per_solve * (V-cycle + residual)."""
+def oracle_step(w, mg, v, sig, chi, t, tol=TOL):
+    """One complete FP64 CPU oracle qs_step in place (predictor, chi update,
+    walls, right-hand side, warm-started multigrid solve to tol, stress
+    correction), timed end to end; returns (seconds, V-cycles)."""
     import oracle as O
-    lam, mu = w.lam, w.mu
+    t0 = time.perf_counter()
+    st, cyc, _ = O.qs_step(mg, v, sig, chi, w.h, w.dt, w.lam, w.mu, O.STZ(**w.stz),
+                           O.BC(**w.bc_values()), t, tol=tol, max_cycles=100)
+    dt = time.perf_counter() - t0
+    if st != 0:
+        raise RuntimeError("oracle qs_step failed with status %d" % st)
+    return dt, cyc
+
+
+def oracle_touch(w, mg, v, sig, chi, t):
+    """A bounded pass over every array of a step (the pointwise pieces and one
+    V-cycle) without advancing the state: the reference arm's warm-up."""
+    import oracle as O
     p = O.STZ(**w.stz)
-    mg = O.MG(w.nx, w.ny, w.nz, lam, mu)
-    v = v.copy()
-    t0 = time.perf_counter()
-    ss, D, sb = O.stress_star(v, sig, chi, w.h, w.dt, mu, p)
+    ss, D, sb = O.stress_star(v, sig, chi, w.h, w.dt, w.mu, p)
     O.chi_update(sig, chi, D, sb, w.h, w.dt, p)
-    O.wall_fill(v, w.h, O.BC(**w.bc_values()), t + w.dt)
-    b = O.div_rhs(ss, w.h, w.dt, mu)
-    O.stress_final(v, ss, w.h, w.dt, lam, mu)
-    t_pw = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    mg.vcycle(b, v)
-    r = O.residual(mg.stencil(0), b, v)
-    O.norm2(r)
-    t_cyc = time.perf_counter() - t0
-    mg.close()
-    return t_pw + cycles_per_solve * t_cyc, t_pw, t_cyc, O.threads()
+    b = O.div_rhs(ss, w.h, w.dt, w.mu)
+    x = v.copy()
+    O.wall_fill(x, w.h, O.BC(**w.bc_values()), t + w.dt)
+    mg.vcycle(b, x)
+    O.stress_final(x, ss, w.h, w.dt, w.lam, w.mu)
+
+
+def rel_err(a, b):
+    """(|a - b|_2 / |b|_2, max|a - b| / max|b|) of two tensors or arrays."""
+    import torch
+    if isinstance(a, torch.Tensor):
+        d = a - b
+        nb, mb = float(torch.linalg.vector_norm(b)), float(b.abs().max())
+        return (float(torch.linalg.vector_norm(d)) / max(nb, 1e-300),
+                float(d.abs().max()) / max(mb, 1e-300))
+    d = a - b
+    return (float(np.linalg.norm(d.ravel())) / max(float(np.linalg.norm(b.ravel())), 1e-300),
+            float(np.abs(d).max()) / max(float(np.abs(b).max()), 1e-300))
 
 
 # ------------------------------------------------------------------ ours
+
+def lockstep(w, ctx_mixed, ctx64, v0, s0, c0, t0, nsteps, stream, dev):
+    """Mixed and FP64 trajectories from the same initial state, one step of
+    each in turn: per-step device times, cycles, and the mixed state's
+    (norm-wise, element-wise) relative error against the FP64 state."""
+    import torch
+
+    from paper_1904_03808_gb300 import make_state
+    st = {}
+    for name in ("mixed", "fp64"):
+        v, sg, c = (torch.from_numpy(a).to(dev) for a in (v0, s0, c0))
+        st[name] = (v, sg, c, make_state(v, sg, c, t0))
+    ctxs = {"mixed": ctx_mixed, "fp64": ctx64}
+    ms = {"mixed": [], "fp64": []}
+    cyc = {"mixed": 0, "fp64": 0}
+    worst = 0.0
+    err = {"v": [], "sigma": [], "chi": []}
+    for _ in range(nsteps):
+        for name in ("mixed", "fp64"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, s = ctxs[name].step(st[name][3], w.dt, TOL)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[name].append(e0.elapsed_time(e1))
+            cyc[name] += s.cycles
+            worst = max(worst, s.rel_resid)
+        for i, key in ((0, "v"), (1, "sigma"), (2, "chi")):
+            err[key].append(rel_err(st["mixed"][i], st["fp64"][i]))
+    del st
+    if nsteps == 0:
+        return {"steps": 0}
+    r3 = lambda x: float("%.3g" % x)  # noqa: E731
+    return {"steps": nsteps, "from": "initial state (t0), both trajectories",
+            "mixed_s_per_step": statistics.mean(ms["mixed"]) / 1e3,
+            "fp64_s_per_step": statistics.mean(ms["fp64"]) / 1e3,
+            "mixed_cycles_per_solve": cyc["mixed"] / nsteps,
+            "fp64_cycles_per_solve": cyc["fp64"] / nsteps, "worst_rel_resid": worst,
+            "max_err_v": max(e[1] for e in err["v"]) if nsteps else None,
+            "max_err_sigma": max(e[1] for e in err["sigma"]) if nsteps else None,
+            "max_err_chi": max(e[1] for e in err["chi"]) if nsteps else None,
+            "err_v_per_step": [r3(e[1]) for e in err["v"]],
+            "err_sigma_per_step": [r3(e[1]) for e in err["sigma"]],
+            "err_note": "max|mixed - fp64| / max|fp64| after each step (element-wise); the "
+                        "norm-wise errors are below these"}
+
+
 
 def run_ours(args):
     import torch
@@ -426,25 +505,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3 / Ke, ws, dev)
     nbytes = (v0.nbytes + s0.nbytes + c0.nbytes)
-    ctx.close()
 
-    # ---- plain FP64 on the same starting state
-    vg.copy_(snap[0])
-    sg.copy_(snap[1])
-    cg.copy_(snap[2])
-    st64 = make_state(vg, sg, cg, snap[3])
+    # ---- C3: mixed and FP64 in lockstep from the initial state, each step's
+    # device time and the mixed state's error against the FP64 one
     ctx64 = mk(MG_FP64)
-    K64 = max(1, min(K, 3))
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    cyc64 = 0
-    for _ in range(K64):
-        _, s = ctx64.step(st64, w.dt, TOL)
-        cyc64 += s.cycles
-    f1.record(stream)
-    torch.cuda.synchronize()
-    t64 = f0.elapsed_time(f1) / 1e3 / K64
+    lock = lockstep(w, ctx, ctx64, v0, s0, c0, t0, args.c3_steps, stream, dev)
+    ctx.close()
 
     # ---- cold solve of a random right-hand side from v = 0 (mixed and FP64)
     from paper_1904_03808_gb300 import inputs as I
@@ -462,19 +528,34 @@ def run_ours(args):
         torch.cuda.synchronize()
         cold[name] = {"s": a0.elapsed_time(a1) / 1e3, "cycles": s.cycles,
                       "outer_iters": s.outer_iters, "rel_resid": s.rel_resid}
-        c.close()
+        if name == "mixed":
+            c.close()
     del bc
 
-    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    # ---- CPU oracle: one complete step from the timed steps' starting state
+    # (rank 0, N = 1 only), beside one FP64 GPU step from the same state
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle as O
         vs, ss_, cs_ = (a.cpu().numpy() for a in snap[:3])
-        cps = cyc64 / K64
-        val, t_pw, t_cyc, thr = oracle_sample(w, vs, ss_, cs_, snap[3], cps)
-        cpu = {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": "FP64 C oracle at %d^3: pointwise step pieces once (%.2f s) + one V-cycle "
-                         "with residual norm (%.2f s), scaled by %.1f FP64 cycles per solve"
-                         % (w.nx, t_pw, t_cyc, cps)}
+        mg = O.MG(w.nx, w.ny, w.nz, w.lam, w.mu)
+        t_cpu, cyc_cpu = oracle_step(w, mg, vs, ss_, cs_, snap[3])
+        mg.close()
+        vg.copy_(snap[0])
+        sg.copy_(snap[1])
+        cg.copy_(snap[2])
+        st64 = make_state(vg, sg, cg, snap[3])
+        ctx64.step(st64, w.dt, TOL)
+        ev, es = rel_err(vg.cpu().numpy(), vs), rel_err(sg.cpu().numpy(), ss_)
+        cpu = {"value": t_cpu, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+               "sample": "one complete FP64 C oracle qs_step at %dx%dx%d (%d V-cycles to rel. "
+                         "resid 1e-10), from the timed steps' starting state, timed end to end "
+                         "(measured, not scaled)" % (w.nx, w.ny, w.nz, cyc_cpu),
+               "gpu_fp64_vs_oracle": {"err_v": ev, "err_sigma": es,
+                                      "note": "(norm-wise, element-wise) relative difference "
+                                              "of the FP64 GPU step from the same state; two "
+                                              "solves to 1e-10 differ by up to cond * 1e-10"}}
+    ctx64.close()
 
     if rank != 0:
         return None
@@ -487,8 +568,12 @@ def run_ours(args):
                              "parallelism": "replicas" if ws > 1 else "single GPU"}),
         "solve": {"cycles_per_solve": cyc / K, "outer_per_solve": outer / K,
                   "worst_rel_resid": worst},
-        "fp64": {"value": t64, "unit": UNIT, "steps": K64, "cycles_per_solve": cyc64 / K64,
-                 "speedup_mixed": t64 / t_step},
+        "fp64": ({"value": lock["fp64_s_per_step"], "unit": UNIT, "steps": lock["steps"],
+                  "cycles_per_solve": lock["fp64_cycles_per_solve"],
+                  "speedup_mixed": lock["fp64_s_per_step"] / lock["mixed_s_per_step"],
+                  "note": "mean over the C3 lockstep steps, mixed timed over the same steps"}
+                 if lock["steps"] else None),
+        "c3": lock,
         "cold_solve": cold,
         "roofline": {"bound": "hbm", "kernel": "finest-level FP32 Gauss-Seidel sweep",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -512,8 +597,11 @@ def I_K():
 # ------------------------------------------------------------- reference arm
 
 def run_reference(args):
-    """The FP64 CPU oracle as it stands, on this host's cores, on a bounded
-    sample per step (see oracle_sample); rank 0 only."""
+    """The FP64 CPU oracle as it stands, on this host's cores: each timed
+    step is one complete oracle qs_step of the 256^3 workload (the oracle's
+    own trajectory from the bench's initial state), timed end to end; each
+    warm-up step a bounded pass over the step's arrays (pointwise pieces and
+    one V-cycle) that leaves the state as it is.  Rank 0 only."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return None
@@ -521,38 +609,201 @@ def run_reference(args):
     O.build()
     w = workload(args.n or 256)
     v, sig, chi, t = w.initial_state()
-    # V-cycles per solve for this workload: one full oracle step at 64^3 of the
-    # same recipe (multigrid cycle counts do not grow with the grid)
-    ws_ = workload(64)
-    vs, ss, cs, ts = ws_.initial_state()
-    mg = O.MG(64, 64, 64, ws_.lam, ws_.mu)
-    st, cps, _ = O.qs_step(mg, vs, ss, cs, ws_.h, ws_.dt, ws_.lam, ws_.mu, O.STZ(**ws_.stz),
-                           O.BC(**ws_.bc_values()), ts, tol=TOL, max_cycles=100)
+    mg = O.MG(w.nx, w.ny, w.nz, w.lam, w.mu)
+    for _ in range(args.warmup):
+        oracle_touch(w, mg, v, sig, chi, t)
+    secs, cycles = [], []
+    for _ in range(args.steps):
+        dt, cyc = oracle_step(w, mg, v, sig, chi, t)
+        t += w.dt
+        secs.append(dt)
+        cycles.append(cyc)
     mg.close()
-    vals = []
-    for k in range(args.warmup + args.steps):
-        val, t_pw, t_cyc, thr = oracle_sample(w, v, sig, chi, t, cps)
-        if k >= args.warmup:
-            vals.append(val)
-    value = float(np.mean(vals))
+    value = float(np.mean(secs))
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
         "data": "synthetic (seeded fields of the paper's recipes)",
         "config": config(w, {"precision": "fp64 (CPU oracle)"}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
-                         "sample": "per step: pointwise pieces at %d^3 + one V-cycle and residual, "
-                                   "scaled by %d cycles per solve (oracle, 64^3 first step)"
-                                   % (w.nx, cps)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                         "sample": "%d complete oracle qs_steps at %dx%dx%d (%.1f V-cycles a "
+                                   "solve), each timed end to end (measured, not scaled); "
+                                   "warm-up: the pointwise pieces and one V-cycle, %d times"
+                                   % (args.steps, w.nx, w.ny, w.nz,
+                                      float(np.mean(cycles)) if cycles else 0.0, args.warmup)},
+        "per_step_s": [float("%.4g" % x) for x in secs],
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+# ------------------------------------------------------------ C2, CPU report, gradient
+
+def run_c2(args):
+    """128^3 cells, 100 FP64 steps of simple shear (strain 2% over the run):
+    the GPU in lockstep with the CPU oracle, the GPU running the oracle's
+    cycle count each step (tol 0), per-step (norm-wise, element-wise)
+    relative difference of v, sigma and chi; both timed.  --preload sets the
+    initial sigma_xz (default 1.2 GPa, the STZ-active variant; 0 is the
+    literal unstressed start, elastic throughout)."""
+    import torch
+
+    import oracle as O
+    from paper_1904_03808_gb300 import MG_FP64, Context, make_state
+    from paper_1904_03808_gb300 import inputs as I
+    n = args.n or 128
+    K = args.steps
+    pre = PRELOAD if args.preload is None else args.preload
+    w = I.Workload(n, steps=K, strain=0.02, preload=pre, chi_mean=600.0, chi_std=30.0,
+                   lc_cells=4.0, seed=2)
+    v, sig, chi, t = w.initial_state()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    vg, sg, cg = (torch.from_numpy(a).to(dev) for a in (v, sig, chi))
+    state = make_state(vg, sg, cg, t)
+    mg = O.MG(w.nx, w.ny, w.nz, w.lam, w.mu)
+    rows = []
+    for k in range(K):
+        t_cpu, cyc = oracle_step(w, mg, v, sig, chi, t)
+        t += w.dt
+        ctx = Context(w.nx, w.ny, w.nz, w.h, I.TABLE1["K"], w.mu, bc=w.bc_values(), stz=w.stz,
+                      precision=MG_FP64, max_cycles=cyc, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, s = ctx.step(state, w.dt, 0.0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.close()
+        row = {"step": k + 1, "cycles": cyc, "oracle_s": t_cpu, "gpu_ms": e0.elapsed_time(e1)}
+        for key, a, b in (("v", vg, v), ("sigma", sg, sig), ("chi", cg, chi)):
+            row["err_" + key] = rel_err(a.cpu().numpy(), b)
+        rows.append(row)
+    mg.close()
+    worst = {key: max(max(r["err_" + key]) for r in rows) for key in ("v", "sigma", "chi")}
+    return {"mode": "c2", "grid": [w.nx, w.ny, w.nz], "steps": K, "preload_pa": pre,
+            "cores": O.threads(),
+            "oracle_s_per_step": statistics.mean(r["oracle_s"] for r in rows),
+            "oracle_s_total": sum(r["oracle_s"] for r in rows),
+            "gpu_ms_per_step": statistics.mean(r["gpu_ms"] for r in rows[1:] or rows),
+            "cycles_per_step": statistics.mean(r["cycles"] for r in rows),
+            "worst_err": worst, "bar": 1e-12,
+            "note": "GPU FP64 steps with the oracle's cycle count each step; err = max of "
+                    "norm-wise and element-wise relative difference",
+            "per_step": [{k: (float("%.3g" % x) if isinstance(x, float) else
+                              [float("%.3g" % y) for y in x] if isinstance(x, tuple) else x)
+                          for k, x in r.items()} for r in rows[::max(1, K // 20)]]}
+
+
+def run_cpu_report(args):
+    """The CPU oracle's complete runs (nothing scaled): a 32^3 single solve of
+    a random right-hand side from v = 0, the 256^3 cold solve and the first 5
+    steps of the bench workload, and the first step of the 512^3 disc
+    workload."""
+    import math
+
+    import oracle as O
+    from paper_1904_03808_gb300 import inputs as I
+    out = {"mode": "cpu-report", "cores": O.threads()}
+    try:
+        out["cpu"] = [ln.split(":", 1)[1].strip() for ln in open("/proc/cpuinfo")
+                      if ln.lower().startswith(("model name", "cpu part"))][:1]
+    except OSError:
+        pass
+
+    def cold(n):
+        b = I.rhs_field(1, n, n, n)
+        x = np.zeros_like(b)
+        x[0, 0], x[0, n] = -1.0, 1.0
+        mg = O.MG(n, n, n, I.lame_lambda(I.TABLE1["K"], I.TABLE1["mu"]), I.TABLE1["mu"])
+        t0 = time.perf_counter()
+        st, cyc, _ = mg.solve(b, x, TOL, 100)
+        dt = time.perf_counter() - t0
+        mg.close()
+        return {"s": dt, "cycles": cyc, "status": st}
+
+    out["c1_32_cold_solve"] = cold(32)
+    out["c3_256_cold_solve"] = cold(256)
+    w = workload(256)
+    v, sig, chi, t = w.initial_state()
+    mg = O.MG(w.nx, w.ny, w.nz, w.lam, w.mu)
+    steps = []
+    for _ in range(5):
+        dt, cyc = oracle_step(w, mg, v, sig, chi, t)
+        t += w.dt
+        steps.append({"s": dt, "cycles": cyc})
+    mg.close()
+    out["c3_256_first_5_steps"] = steps
+    del v, sig, chi
+    w5 = I.Workload(512, steps=20, kind=1, chi_mean=600.0, chi_std=30.0, lc_cells=8.0, seed=5,
+                    dt_ts=2.0e3)
+    w5.omega = 2.0 * math.pi / (1.0e8 * w5.ts)
+    v, sig, chi, t = w5.initial_state()
+    mg = O.MG(w5.nx, w5.ny, w5.nz, w5.lam, w5.mu)
+    dt, cyc = oracle_step(w5, mg, v, sig, chi, t)
+    mg.close()
+    out["c5_512_first_step"] = {"s": dt, "cycles": cyc,
+                                "workload": "disc kind 1, chi0 600 K / 30 K / l_c = 8 cells, "
+                                            "dt = 2e3 t_s, from rest"}
+    return out
+
+
+def run_grad(args):
+    """The differentiation workload: 64^3 cells, 40 FP64 steps of simple
+    shear from the STZ-active preload; the plastic work W alone
+    (qs_plastic_work, no checkpoints) and W with dW/dchi0
+    (qs_plastic_work_grad, checkpoints every --every steps), device times."""
+    import torch
+
+    from paper_1904_03808_gb300 import MG_FP64, MG_MIXED, Context, make_state
+    from paper_1904_03808_gb300 import inputs as I
+    n = args.n or 64
+    K = args.steps if args.steps != 20 else 40
+    w = I.Workload(n, steps=K, strain=0.02, preload=PRELOAD, chi_mean=600.0, chi_std=30.0,
+                   lc_cells=4.0, seed=4)
+    v, sig, chi, t = w.initial_state()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    out = {"mode": "grad", "grid": [w.nx, w.ny, w.nz], "steps": K, "checkpoint_every": args.every,
+           "tol": TOL}
+    for name, prec in (("fp64", MG_FP64), ("mixed", MG_MIXED)):
+        ctx = Context(w.nx, w.ny, w.nz, w.h, I.TABLE1["K"], w.mu, bc=w.bc_values(), stz=w.stz,
+                      precision=prec, max_cycles=100, stream=stream)
+        res = {}
+        for rep in range(2):  # the first round warms the code paths up
+            for what in ("forward", "gradient"):
+                vg, sg, cg = (torch.from_numpy(a).to(dev) for a in (v, sig, chi))
+                state = make_state(vg, sg, cg, t)
+                grad = torch.zeros_like(cg)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if what == "forward":
+                    _, W, _ = ctx.plastic_work(state, K, w.dt, tol=TOL, checkpoint_every=K)
+                else:
+                    _, W, _ = ctx.plastic_work_grad(state, K, w.dt, grad, tol=TOL,
+                                                    checkpoint_every=args.every)
+                torch.cuda.synchronize()
+                res[what] = {"s": time.perf_counter() - t0, "W": W}
+                if what == "gradient":
+                    res[what]["max_abs_grad"] = float(grad.abs().max())
+        res["gradient_over_forward"] = res["gradient"]["s"] / res["forward"]["s"]
+        out[name] = res
+        ctx.close()
+    out["note"] = ("host wall time of each call (each synchronises its stream); the gradient "
+                   "call runs the forward steps with checkpoints, recomputes each segment and "
+                   "runs the adjoint steps, each with one adjoint solve")
+    return out
 
 
 def main():
     args = parse()
     if args.sweep_only:
         out = run_sweeps(args)
+    elif args.c2:
+        out = run_c2(args)
+    elif args.cpu_report:
+        out = run_cpu_report(args)
+    elif args.grad:
+        out = run_grad(args)
     elif args.disc:
         out = run_disc(args)
     else:

@@ -56,7 +56,8 @@ enum { MG_FP64 = 0, MG_MIXED = 1 };
 /* mg_opts.flags */
 enum {
     MG_FLAG_COLOUR_PASSES = 1, /* FP32 sweeps: one launch per colour */
-    MG_FLAG_NO_GRAPH = 2       /* FP32 inner cycles: plain launches, no CUDA graph */
+    MG_FLAG_NO_GRAPH = 2,      /* FP32 inner cycles: plain launches, no CUDA graph */
+    MG_FLAG_TWO_PHASE = 4      /* finest FP32 sweeps: one launch per k-parity */
 };
 enum { MG_HIST = 128 };
 
@@ -103,7 +104,10 @@ typedef struct {
  *                 eight colour launches instead of the two-phase kernels
  *                 (row strips, whole planes, tiles); MG_FLAG_NO_GRAPH issues the FP32 inner cycles as
  *                 plain launches instead of replaying a CUDA graph captured
- *                 at their first use (same arithmetic; kept for comparison).
+ *                 at their first use; MG_FLAG_TWO_PHASE runs the finest-level
+ *                 FP32 sweep as two launches (the planes of one k-parity,
+ *                 then the other) where the fused one-launch sweep would
+ *                 apply (same arithmetic; kept for comparison).
  */
 typedef struct {
     int precision;
@@ -275,21 +279,54 @@ mg_status qs_step_adjoint(mg_ctx *ctx, const qs_state *state, double dt, double 
                           mg_stats *stats);
 
 /*
- * qs_plastic_work_grad -- W = the plastic work of nsteps qs_steps from
- * `state` (sum over steps and cells of 2 D^pl sbar dt h^3, D^pl and sbar of
- * the state each step starts from), and dW/dchi0, the derivative with respect
- * to the initial chi field.  Runs the steps forward (state is left at the
- * final state, as after nsteps qs_step calls), keeping a copy of the state
- * every checkpoint_every steps, then runs qs_step_adjoint backwards one
- * segment at a time, recomputing the segment's states from its checkpoint
- * (the forward kernels and reductions are deterministic, so the recomputed
- * states equal the first ones bit for bit).
- *   chibar: device (nz, ny, nx), receives dW/dchi0.
+ * qs_plastic_work -- the forward half of qs_plastic_work_grad: W = the
+ * plastic work of nsteps qs_steps from `state` (sum over steps and cells of
+ * 2 D^pl sbar dt h^3 -- the plastic power of Eq. 26's growth term -- with
+ * D^pl and sbar of the state each step starts from); state is left at the
+ * final state, as after nsteps qs_step calls.
+ *   checkpoints: device, caller-owned, or NULL.  If given, it receives a copy
+ *       of the state every checkpoint_every steps (steps 0, k, 2k, ...):
+ *       ceil(nsteps / k) blocks of 3 (nz+1) ny nx + 7 nz ny nx doubles, each
+ *       v (3, nz+1, ny, nx), then sigma (6, nz, ny, nx), then chi (nz, ny, nx).
+ *       qs_plastic_work_backward takes it.
  *   work: host, receives W.
  *   stats: the last solve's statistics (may be NULL).
- * Device memory: ceil(nsteps / checkpoint_every) + checkpoint_every state
- * copies (10 doubles a cell each) plus two adjoint arrays, allocated for the
- * call and freed before it returns.
+ * Makes no state copies of its own.  Errors: as qs_step; MG_ERR_ARG for nsteps < 1,
+ * checkpoint_every < 1, or a context without stz/bc parameters.
+ */
+mg_status qs_plastic_work(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
+                          int checkpoint_every, double *checkpoints, double *work,
+                          mg_stats *stats);
+
+/*
+ * qs_plastic_work_backward -- the reverse half: dW/dchi0 from the checkpoints
+ * a qs_plastic_work call wrote with the same nsteps, dt, tol and
+ * checkpoint_every, its state having started at time t0 and step count
+ * step0.  Runs qs_step_adjoint backwards one segment at a time, recomputing
+ * the segment's states from its checkpoint (the forward kernels and
+ * reductions are deterministic and the times are re-accumulated from t0 as
+ * the forward steps did, so the recomputed states equal the first ones bit
+ * for bit).
+ *   checkpoints: device, as written by qs_plastic_work; not modified.
+ *   chibar: device (nz, ny, nx), receives dW/dchi0.
+ *   stats: the last adjoint solve's statistics (may be NULL).
+ * Device memory: checkpoint_every state copies plus two adjoint arrays,
+ * allocated for the call and freed before it returns, and the context's
+ * adjoint scratch (qs_step_adjoint).
+ * Errors: as qs_step and qs_step_adjoint, MG_ERR_ARG as qs_plastic_work.
+ */
+mg_status qs_plastic_work_backward(mg_ctx *ctx, const double *checkpoints, double t0, long step0,
+                                   int nsteps, double dt, double tol, int checkpoint_every,
+                                   double *chibar, mg_stats *stats);
+
+/*
+ * qs_plastic_work_grad -- qs_plastic_work and qs_plastic_work_backward in one
+ * call: W (host `work`) and dW/dchi0 (device `chibar`, (nz, ny, nx)), the
+ * derivative of the plastic work of nsteps steps with respect to the initial
+ * chi field.  state is left at the final state.  The checkpoints, every
+ * checkpoint_every steps, are allocated for the call and freed before it
+ * returns (ceil(nsteps / checkpoint_every) + checkpoint_every state copies,
+ * 10 doubles a cell each, plus two adjoint arrays).
  * Errors: as qs_step and qs_step_adjoint, MG_ERR_ARG for nsteps < 1 or
  * checkpoint_every < 1.
  */
@@ -338,9 +375,10 @@ long mg_launch_count(void);
  * exceed 2097152 (e.g. 64^3 fits, 96^3 does not); larger grids return
  * MG_ERR_SHAPE with a message.  Every GPU that loads the library holds the
  * array until the process exits.
- * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress; nothing is cached, so a cudaDeviceReset in between
+ * does no harm).  The first call on a device may load the library's device
+ * code there; make that first call before any stream capture.
  * All calls share the one array, which keeps the last call's residual (every
  * value a call reads was written by the same call): calls that overlap on the
  * GPU, from other streams or host threads, race on it, so serialise them.

@@ -26,13 +26,26 @@ _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
 
 
+# -O3 without -march=native and without contraction into fused multiply-adds,
+# so that the oracle computes the expressions as written and gives the same
+# rounding on every host (x86-64 and aarch64 alike)
+_CFLAGS = ["-O3", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC"]
+
+
 def build(force: bool = False) -> str:
-    """Compile qs_oracle.c with gcc (OpenMP inside colour passes)."""
+    """Compile qs_oracle.c with gcc (OpenMP across the nodes of one colour
+    pass and of one pointwise loop)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+    stamp = _OUT + ".flags"
+    flags = " ".join(_CFLAGS)
+    stale = (not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC) or
+             not os.path.exists(stamp) or open(stamp).read() != flags)
+    if force or stale:
         tmp = _OUT + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc"] + _CFLAGS + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
+        with open(stamp, "w") as f:
+            f.write(flags)
     return _OUT
 
 

@@ -21,6 +21,7 @@ MG_OK, MG_ERR_ARG, MG_ERR_SHAPE, MG_ERR_CUDA, MG_ERR_OOM, MG_ERR_NOCONV, MG_ERR_
 MG_FP64, MG_MIXED = 0, 1
 MG_FLAG_COLOUR_PASSES = 1
 MG_FLAG_NO_GRAPH = 2
+MG_FLAG_TWO_PHASE = 4
 MG_HIST = 128
 
 
@@ -92,6 +93,10 @@ _SIGS = {
                                   _P, _P, _P, C.POINTER(mg_stats)]),
     "qs_plastic_work_grad": (C.c_int, [_P, C.POINTER(qs_state), C.c_int, C.c_double, C.c_double,
                                        C.c_int, _P, C.POINTER(C.c_double), C.POINTER(mg_stats)]),
+    "qs_plastic_work": (C.c_int, [_P, C.POINTER(qs_state), C.c_int, C.c_double, C.c_double,
+                                  C.c_int, _P, C.POINTER(C.c_double), C.POINTER(mg_stats)]),
+    "qs_plastic_work_backward": (C.c_int, [_P, _P, C.c_double, C.c_long, C.c_int, C.c_double,
+                                           C.c_double, C.c_int, _P, C.POINTER(mg_stats)]),
     "mg_profile": (C.c_int, [_P, C.c_int]),
     "mg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_long),
                                   C.POINTER(C.c_long)]),
@@ -240,6 +245,44 @@ class Context:
             _check(st, "qs_plastic_work_grad")
         return st, W.value, s
 
+    def checkpoint_size(self, nsteps, checkpoint_every):
+        """Doubles of the checkpoint buffer qs_plastic_work fills."""
+        nx, ny, nz = self.shape
+        seg = min(int(checkpoint_every), int(nsteps))
+        ncp = (int(nsteps) + seg - 1) // seg
+        return ncp * (3 * (nz + 1) * ny * nx + 7 * nz * ny * nx)
+
+    def plastic_work(self, state: qs_state, nsteps, dt, tol=1e-10, checkpoint_every=8,
+                     checkpoints=None, raise_on_error=True):
+        """qs_plastic_work: returns (status, W, stats); state is advanced by
+        nsteps steps; checkpoints (float64 CUDA tensor of checkpoint_size
+        doubles, or None) receives a copy of the state every checkpoint_every
+        steps."""
+        s = mg_stats()
+        W = C.c_double()
+        if checkpoints is not None and checkpoints.numel() < self.checkpoint_size(
+                nsteps, checkpoint_every):
+            raise ValueError("checkpoint buffer too small")
+        st = lib().qs_plastic_work(self.h, C.byref(state), int(nsteps), dt, tol,
+                                   int(checkpoint_every), _ptr(checkpoints), C.byref(W), C.byref(s))
+        if raise_on_error:
+            _check(st, "qs_plastic_work")
+        return st, W.value, s
+
+    def plastic_work_backward(self, checkpoints, t0, step0, nsteps, dt, chibar, tol=1e-10,
+                              checkpoint_every=8, raise_on_error=True):
+        """qs_plastic_work_backward: chibar receives dW/dchi0 from the
+        checkpoints of a plastic_work call with the same arguments."""
+        s = mg_stats()
+        if checkpoints.numel() < self.checkpoint_size(nsteps, checkpoint_every):
+            raise ValueError("checkpoint buffer too small")
+        st = lib().qs_plastic_work_backward(self.h, _ptr(checkpoints), float(t0), int(step0),
+                                            int(nsteps), dt, tol, int(checkpoint_every),
+                                            _ptr(chibar), C.byref(s))
+        if raise_on_error:
+            _check(st, "qs_plastic_work_backward")
+        return st, s
+
     def profile(self, enable=True):
         _check(lib().mg_profile(self.h, int(enable)), "mg_profile")
 
@@ -302,7 +345,10 @@ class Context:
 def plastic_work(ctx: "Context", v0, sigma0, chi0, t0, nsteps, dt, tol=1e-10, checkpoint_every=8):
     """The plastic work W of nsteps projection steps from (v0, sigma0, chi0)
     at time t0, differentiable with respect to chi0 (a torch.autograd.Function
-    over qs_plastic_work_grad; the inputs are copied, not advanced)."""
+    over qs_plastic_work / qs_plastic_work_backward; the inputs are copied,
+    not advanced).  The forward pass runs the steps only, keeping checkpoints
+    when chi0 requires a gradient; the backward pass runs the reverse sweep
+    from them."""
     return _PlasticWork.apply(chi0, ctx, v0, sigma0, t0, nsteps, dt, tol, checkpoint_every)
 
 
@@ -312,19 +358,37 @@ def _plastic_work_class():
     class PlasticWork(torch.autograd.Function):
         @staticmethod
         def forward(fctx, chi0, ctx, v0, sigma0, t0, nsteps, dt, tol, checkpoint_every):
-            v = v0.detach().clone()
-            sig = sigma0.detach().clone()
-            chi = chi0.detach().clone()
-            state = make_state(v, sig, chi, t0)
-            grad = torch.zeros_like(chi)
-            _, W, _ = ctx.plastic_work_grad(state, nsteps, dt, grad, tol=tol,
-                                            checkpoint_every=checkpoint_every)
-            fctx.save_for_backward(grad)
+            # the library works on ctx.stream: order it after the work that
+            # produced the inputs and the copies below on the current stream
+            with torch.cuda.stream(ctx.stream):
+                ctx.stream.wait_stream(torch.cuda.current_stream(chi0.device))
+                v = v0.detach().clone()
+                sig = sigma0.detach().clone()
+                chi = chi0.detach().clone()
+                cp = None
+                if fctx.needs_input_grad[0]:
+                    cp = torch.empty(ctx.checkpoint_size(nsteps, checkpoint_every),
+                                     dtype=torch.float64, device=chi0.device)
+                state = make_state(v, sig, chi, t0)
+                _, W, _ = ctx.plastic_work(state, nsteps, dt, tol=tol,
+                                           checkpoint_every=checkpoint_every, checkpoints=cp)
+            fctx.lib_ctx = ctx
+            fctx.args = (t0, nsteps, dt, tol, checkpoint_every)
+            if cp is not None:
+                fctx.save_for_backward(cp)
             return torch.tensor(W, dtype=torch.float64, device=chi0.device)
 
         @staticmethod
         def backward(fctx, gW):
-            (grad,) = fctx.saved_tensors
+            (cp,) = fctx.saved_tensors
+            ctx = fctx.lib_ctx
+            t0, nsteps, dt, tol, every = fctx.args
+            with torch.cuda.stream(ctx.stream):
+                ctx.stream.wait_stream(torch.cuda.current_stream(cp.device))
+                grad = torch.empty(ctx.shape[::-1], dtype=torch.float64, device=cp.device)
+                ctx.plastic_work_backward(cp, t0, 0, nsteps, dt, grad, tol=tol,
+                                          checkpoint_every=every)
+            torch.cuda.current_stream(cp.device).wait_stream(ctx.stream)
             return (gW * grad,) + (None,) * 8
 
     return PlasticWork

@@ -70,38 +70,28 @@ __device__ __forceinline__ void fine_off(const T *x, const Dims &d, int i0, int 
 #undef MYZ
 }
 
-// general 27-point block stencil, off-centre part
+// coarse 27-point block stencil, off-centre part, in parity-class form
 template <typename T>
 __device__ __forceinline__ void coarse_off(const T *x, const Dims &d, int i, int j, int k,
                                            const Coarse<T> &c, T o[3]) {
     const int nx = d.nx, ny = d.ny;
-    T s0 = 0, s1 = 0, s2 = 0;
-#pragma unroll
-    for (int dz = -1; dz <= 1; dz++) {
-        const long pl = (long)(k + dz) * ny;
-#pragma unroll
-        for (int dy = -1; dy <= 1; dy++) {
-            int jj = j + dy;
-            jj = jj < 0 ? jj + ny : (jj >= ny ? jj - ny : jj);
-            const long row = (pl + jj) * nx;
-#pragma unroll
-            for (int dx = -1; dx <= 1; dx++) {
-                const int dd = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-                if (dd == 13) continue;
-                int ii = i + dx;
-                ii = ii < 0 ? ii + nx : (ii >= nx ? ii - nx : ii);
-                const long q = row + ii;
-                const T v0 = x[q], v1 = x[q + d.cs], v2 = x[q + 2 * d.cs];
-                const T *s = c.S + dd * 9;
-                s0 += s[0] * v0 + s[1] * v1 + s[2] * v2;
-                s1 += s[3] * v0 + s[4] * v1 + s[5] * v2;
-                s2 += s[6] * v0 + s[7] * v1 + s[8] * v2;
-            }
-        }
-    }
-    o[0] = s0;
-    o[1] = s1;
-    o[2] = s2;
+    const long ps = (long)nx * ny;
+    const int im = i ? i - 1 : nx - 1, ip = i + 1 < nx ? i + 1 : 0;
+    const int jm = j ? j - 1 : ny - 1, jp = j + 1 < ny ? j + 1 : 0;
+    const int col[3] = {im, i, ip};
+    const long row[3] = {(long)jm * nx, (long)j * nx, (long)jp * nx};
+    const long pc = (long)k * ps;
+    auto u = [&](int b, int dx, int dy) -> T {
+        return x[b * d.cs + pc + row[dy + 1] + col[dx + 1]];
+    };
+    auto sd = [&](int b, int dx, int dy, T &S, T &D) {
+        const long q = b * d.cs + pc + row[dy + 1] + col[dx + 1];
+        const T lo = x[q - ps], hi = x[q + ps];
+        S = hi + lo;
+        D = hi - lo;
+    };
+    coarse_plane_terms(c, u, o);
+    coarse_z_terms(c, sd, o);
 }
 
 // launch shape of the node kernels: 32 x 8 threads over (i, j), grid.z over
@@ -153,10 +143,8 @@ __global__ void k_gs_coarse(Dims d, Coarse<T> c, const T *__restrict__ b, T *x, 
     T o[3];
     coarse_off<T>(x, d, i, j, k, c, o);
     const long p = ((long)k * d.ny + j) * d.nx + i;
-    const T f0 = b[p] - o[0], f1 = b[p + d.cs] - o[1], f2 = b[p + 2 * d.cs] - o[2];
-    x[p] = c.Dinv[0] * f0 + c.Dinv[1] * f1 + c.Dinv[2] * f2;
-    x[p + d.cs] = c.Dinv[3] * f0 + c.Dinv[4] * f1 + c.Dinv[5] * f2;
-    x[p + 2 * d.cs] = c.Dinv[6] * f0 + c.Dinv[7] * f1 + c.Dinv[8] * f2;
+#pragma unroll
+    for (int a = 0; a < 3; a++) x[p + a * d.cs] = c.dinv[a] * (b[p + a * d.cs] - o[a]);
 }
 
 template <typename T>
@@ -179,11 +167,9 @@ __global__ void k_res_coarse(Dims d, Coarse<T> c, const T *__restrict__ b,
     T o[3];
     coarse_off<T>(x, d, i, j, k, c, o);
     const long p = ((long)k * d.ny + j) * d.nx + i;
-    const T x0 = x[p], x1 = x[p + d.cs], x2 = x[p + 2 * d.cs];
-    const T *s = c.S + 13 * 9;
-    r[p] = b[p] - (o[0] + s[0] * x0 + s[1] * x1 + s[2] * x2);
-    r[p + d.cs] = b[p + d.cs] - (o[1] + s[3] * x0 + s[4] * x1 + s[5] * x2);
-    r[p + 2 * d.cs] = b[p + 2 * d.cs] - (o[2] + s[6] * x0 + s[7] * x1 + s[8] * x2);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        r[p + a * d.cs] = b[p + a * d.cs] - (o[a] + c.cd[a][0] * x[p + a * d.cs]);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -75,6 +75,10 @@ struct mg_ctx {
     double *Ainv;
     int ncoarse;
     double *partials, *dsum, *hsum;
+    // cross-CTA state of the fused finest-level sweep (when it applies)
+    SweepSync sync;
+    bool has_sync;
+    int *herr;  // pinned host copy of its error word
     double *sig_star, *dpl, *sbar, *chi_tmp, *rhs;
     // adjoint-step scratch, allocated at the first qs_step_adjoint
     double *adj_rhs, *adj_lam, *adj_cb, *adj_db, *adj_sbb, *adj_sgb, *adj_Lb;
@@ -180,21 +184,54 @@ void galerkin_table(const double *Sf, double *Sc) {
             }
 }
 
-bool invert3(const double *M, double *Mi) {
-    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8],
-                 c02 = M[3] * M[7] - M[4] * M[6];
-    const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
-    if (!(fabs(det) > 0.0)) return false;
-    const double id = 1.0 / det;
-    Mi[0] = c00 * id;
-    Mi[1] = (M[2] * M[7] - M[1] * M[8]) * id;
-    Mi[2] = (M[1] * M[5] - M[2] * M[4]) * id;
-    Mi[3] = c01 * id;
-    Mi[4] = (M[0] * M[8] - M[2] * M[6]) * id;
-    Mi[5] = (M[2] * M[3] - M[0] * M[5]) * id;
-    Mi[6] = c02 * id;
-    Mi[7] = (M[1] * M[6] - M[0] * M[7]) * id;
-    Mi[8] = (M[0] * M[4] - M[1] * M[3]) * id;
+// Parity-class form of a 27 x 3 x 3 stencil table (see Coarse<T>): the
+// class values are the means of their members; false when an entry departs
+// from its class value by more than 1e-12 of the largest entry (a table
+// without the reflection symmetry) or a centre entry is not positive
+bool parity_classes(const double *S, Coarse<double> &c) {
+    double mx = 0.0;
+    for (int m = 0; m < 243; m++) mx = fmax(mx, fabs(S[m]));
+    double cs[3][8] = {}, gs[3][2] = {};
+    int cn[3][8] = {}, gn[3][2] = {};
+    auto sgn = [](int v) { return v > 0 ? 1.0 : -1.0; };
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                const int dd = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1), dv[3] = {dx, dy, dz};
+                const int cls = abs(dx) + 2 * abs(dy) + 4 * abs(dz);
+                for (int a = 0; a < 3; a++) {
+                    cs[a][cls] += S[dd * 9 + 4 * a];
+                    cn[a][cls]++;
+                    for (int b = 0; b < 3; b++)
+                        if (b != a && dv[a] && dv[b]) {
+                            const int t = 3 - a - b;
+                            gs[t][abs(dv[t])] += sgn(dv[a]) * sgn(dv[b]) * S[dd * 9 + 3 * a + b];
+                            gn[t][abs(dv[t])]++;
+                        }
+                }
+            }
+    for (int a = 0; a < 3; a++) {
+        for (int m = 0; m < 8; m++) c.cd[a][m] = cs[a][m] / cn[a][m];
+        for (int m = 0; m < 2; m++) c.g[a][m] = gs[a][m] / gn[a][m];
+        if (!(c.cd[a][0] > 0.0)) return false;
+        c.dinv[a] = 1.0 / c.cd[a][0];
+    }
+    // every entry against the value its class gives it
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                const int dd = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1), dv[3] = {dx, dy, dz};
+                const int cls = abs(dx) + 2 * abs(dy) + 4 * abs(dz);
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++) {
+                        double want = 0.0;
+                        if (a == b)
+                            want = c.cd[a][cls];
+                        else if (dv[a] && dv[b])
+                            want = sgn(dv[a]) * sgn(dv[b]) * c.g[3 - a - b][abs(dv[3 - a - b])];
+                        if (fabs(S[dd * 9 + 3 * a + b] - want) > 1e-12 * mx) return false;
+                    }
+            }
     return true;
 }
 
@@ -294,11 +331,24 @@ mg_status prof_drain(mg_ctx *ctx) {
 // ---------------------------------------------------------------- norms
 
 // ||r||^2 from the partial sums of the last reduction kernel
+// the fused sweep's error word (set when a bounded wait for a neighbouring
+// tile gave up), read after the stream has drained; cleared when reported
+mg_status sync_error(mg_ctx *ctx) {
+    if (!ctx->has_sync || !*ctx->herr) return MG_OK;
+    *ctx->herr = 0;
+    CK(cudaMemsetAsync(ctx->sync.err, 0, sizeof(int), ctx->st));
+    set_err("fused Gauss-Seidel sweep: a wait for a neighbouring tile gave up");
+    return MG_ERR_CUDA;
+}
+
 mg_status read_sum(mg_ctx *ctx, double *out) {
     CK(sum_partials(ctx->partials, ctx->dsum, ctx->st));
     CK(cudaMemcpyAsync(ctx->hsum, ctx->dsum, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    if (ctx->has_sync)
+        CK(cudaMemcpyAsync(ctx->herr, ctx->sync.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     *out = ctx->hsum[0];
+    CKS(sync_error(ctx));
     return prof_drain(ctx);
 }
 
@@ -361,7 +411,8 @@ mg_status sweeps_tiled(mg_ctx *ctx, int l, const float *b, float *x, int sweeps,
     }
     for (int s = 0; s < sweeps; s++) {
         if (l == 0)
-            CK(gs_sweep_fine_tiled(d, ctx->f32, b, a, o, descending, ctx->st, ctx->split0));
+            CK(gs_sweep_fine_tiled(d, ctx->f32, b, a, o, descending, ctx->st, ctx->split0,
+                                   ctx->has_sync ? &ctx->sync : nullptr));
         else
             CK(gs_sweep_coarse_tiled(d, ctx->c32[l], b, a, o, descending, ctx->st));
         float *t = a;
@@ -755,6 +806,7 @@ void mg_free(mg_ctx *ctx) {
     else cudaDeviceSynchronize();
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->hsum) cudaFreeHost(ctx->hsum);
+    if (ctx->herr) cudaFreeHost(ctx->herr);
     if (ctx->prof_events)
         for (int i = 0; i < kProfSlots; i++) {
             cudaEventDestroy(ctx->ev[i][0]);
@@ -846,19 +898,18 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
     ctx->f32.kq = (float)kq;
     ctx->f32.dinv = (float)ctx->f64.dinv;
     for (int l = 0; l < ctx->nlev; l++) {
-        double Di[9];
-        if (!invert3(ctx->S[l] + 13 * 9, Di)) {
-            set_err("mg_setup: singular centre block on level %d", l);
+        if (!parity_classes(ctx->S[l], ctx->c64[l])) {
+            set_err("mg_setup: the level-%d operator lacks the reflection symmetry of its "
+                    "parity-class form, or has a singular centre block", l);
             delete ctx;
             return MG_ERR_ARG;
         }
-        for (int m = 0; m < 243; m++) {
-            ctx->c64[l].S[m] = ctx->S[l][m];
-            ctx->c32[l].S[m] = (float)ctx->S[l][m];
-        }
-        for (int m = 0; m < 9; m++) {
-            ctx->c64[l].Dinv[m] = Di[m];
-            ctx->c32[l].Dinv[m] = (float)Di[m];
+        const Coarse<double> &c = ctx->c64[l];
+        Coarse<float> &f = ctx->c32[l];
+        for (int a = 0; a < 3; a++) {
+            for (int m = 0; m < 8; m++) f.cd[a][m] = (float)c.cd[a][m];
+            for (int m = 0; m < 2; m++) f.g[a][m] = (float)c.g[a][m];
+            f.dinv[a] = (float)c.dinv[a];
         }
     }
     std::vector<double> Ainv;
@@ -905,6 +956,25 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         ALLOC(ctx->sbar, nc);
         ALLOC(ctx->chi_tmp, nc);
         ALLOC(ctx->rhs, corner_count(ctx->L[0]));
+    }
+    {
+        long na = 0, np_ = 0, nb = 0;
+        if (!(opts->flags & (MG_FLAG_COLOUR_PASSES | MG_FLAG_TWO_PHASE)) && ctx->nlev > 1 &&
+            fused_sweep_sizes(ctx->L[0], na, np_, nb)) {
+            ALLOC(ctx->sync.aflag, (size_t)na);
+            ALLOC(ctx->sync.pflag, (size_t)np_);
+            ALLOC(ctx->sync.xbuf, (size_t)nb);
+            ALLOC(ctx->sync.epoch, (size_t)1);
+            ALLOC(ctx->sync.done, (size_t)1);
+            ALLOC(ctx->sync.err, (size_t)1);
+            if (cudaMallocHost((void **)&ctx->herr, sizeof(int)) != cudaSuccess) {
+                set_err("cudaMallocHost failed");
+                s = MG_ERR_OOM;
+                goto fail;
+            }
+            *ctx->herr = 0;
+            ctx->has_sync = true;
+        }
     }
 #undef ALLOC
     if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1070,8 +1140,10 @@ mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps,
     } else {
         CKS(smooth<float>(ctx, level, (const float *)b, (float *)x, nsweeps, descending != 0));
     }
+    if (ctx->has_sync)
+        CK(cudaMemcpyAsync(ctx->herr, ctx->sync.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    return MG_OK;
+    return sync_error(ctx);
 }
 
 mg_status mg_restrict(mg_ctx *ctx, int level, const double *r, double *bc) {
@@ -1227,60 +1299,68 @@ struct StateStore {
 
 }  // namespace
 
-mg_status qs_plastic_work_grad(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
-                               int checkpoint_every, double *chibar, double *work,
-                               mg_stats *stats) {
+namespace {
+
+size_t state_doubles(const Dims &d) { return corner_count(d) + 7 * (size_t)d.nx * d.ny * d.nz; }
+
+cudaError_t copy_state(mg_ctx *ctx, const qs_state &from, qs_state &to) {
+    const Dims &d = ctx->L[0];
+    const size_t nc = (size_t)d.nx * d.ny * d.nz, nv = corner_count(d);
+    cudaError_t e = cudaMemcpyAsync(to.v, from.v, nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    ctx->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(to.sigma, from.sigma, 6 * nc * sizeof(double),
+                            cudaMemcpyDeviceToDevice, ctx->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(to.chi, from.chi, nc * sizeof(double), cudaMemcpyDeviceToDevice,
+                            ctx->st);
+    to.t = from.t;
+    to.step = from.step;
+    return e;
+}
+
+// checkpoint c of a contiguous block of states: v, then sigma, then chi
+qs_state checkpoint_view(mg_ctx *ctx, const double *base, int c) {
+    const Dims &d = ctx->L[0];
+    const size_t nc = (size_t)d.nx * d.ny * d.nz, nv = corner_count(d);
+    double *q = const_cast<double *>(base) + (size_t)c * state_doubles(d);
+    qs_state s;
+    s.v = q;
+    s.sigma = q + nv;
+    s.chi = q + nv + 6 * nc;
+    s.t = 0.0;
+    s.step = 0;
+    return s;
+}
+
+mg_status work_args(mg_ctx *ctx, const void *state, int nsteps, double dt, int checkpoint_every,
+                    const char *who) {
     CKS(check_ctx(ctx));
-    if (!state || !state->v || !state->sigma || !state->chi || !chibar || !work ||
-        nsteps < 1 || checkpoint_every < 1 || !(dt > 0.0)) {
-        set_err("qs_plastic_work_grad: null array, nsteps < 1, checkpoint_every < 1 or dt <= 0");
+    if (!state || nsteps < 1 || checkpoint_every < 1 || !(dt > 0.0)) {
+        set_err("%s: null argument, nsteps < 1, checkpoint_every < 1 or dt <= 0", who);
         return MG_ERR_ARG;
     }
     if (!ctx->has_stz || !ctx->has_bc) {
-        set_err("qs_plastic_work_grad: context was set up without stz/bc parameters");
+        set_err("%s: context was set up without stz/bc parameters", who);
         return MG_ERR_ARG;
     }
+    return MG_OK;
+}
+
+// forward steps summing the plastic work of each (D^pl and sbar of the state
+// the step starts from), keeping a copy of the state every `seg` steps in
+// cp (may be null)
+mg_status work_forward(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol, int seg,
+                       double *cp, double *work, mg_stats *stats) {
     const Dims &d = ctx->L[0];
-    const size_t nc = (size_t)d.nx * d.ny * d.nz, nv = corner_count(d);
-    const int seg = checkpoint_every < nsteps ? checkpoint_every : nsteps;
-    const int ncp = (nsteps + seg - 1) / seg;
-    StateStore store;
-    // checkpoints (every seg steps) and the states of one segment
-    std::vector<qs_state> cp(ncp), ss(seg);
-    for (int c = 0; c < ncp + seg; c++) {
-        qs_state &q = c < ncp ? cp[c] : ss[c - ncp];
-        q.v = store.get(nv);
-        q.sigma = store.get(6 * nc);
-        q.chi = store.get(nc);
-        if (!q.v || !q.sigma || !q.chi) {
-            set_err("qs_plastic_work_grad: out of device memory for %d checkpoints", ncp + seg);
-            return MG_ERR_OOM;
-        }
-    }
-    double *vbar = store.get(nv), *sigbar = store.get(6 * nc);
-    if (!vbar || !sigbar) {
-        set_err("qs_plastic_work_grad: out of device memory");
-        return MG_ERR_OOM;
-    }
-    auto copy_state = [&](const qs_state &from, qs_state &to) -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(to.v, from.v, nv * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, ctx->st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(to.sigma, from.sigma, 6 * nc * sizeof(double),
-                                cudaMemcpyDeviceToDevice, ctx->st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(to.chi, from.chi, nc * sizeof(double), cudaMemcpyDeviceToDevice,
-                                ctx->st);
-        to.t = from.t;
-        to.step = from.step;
-        return e;
-    };
-    // forward, keeping checkpoints and summing the plastic work of each step
-    // (D^pl and sbar of the state the step starts from)
+    const size_t nc = (size_t)d.nx * d.ny * d.nz;
     const double wscale = 2.0 * dt * ctx->h * ctx->h * ctx->h;
     double W = 0.0;
     for (int n = 0; n < nsteps; n++) {
-        if (n % seg == 0) CK(copy_state(*state, cp[n / seg]));
+        if (cp && n % seg == 0) {
+            qs_state q = checkpoint_view(ctx, cp, n / seg);
+            CK(copy_state(ctx, *state, q));
+        }
         const mg_status s = qs_step(ctx, state, dt, tol, stats);
         if (s != MG_OK) return s;
         CK(dot_cells(ctx->dpl, ctx->sbar, (long)nc, ctx->partials, ctx->st));
@@ -1290,15 +1370,54 @@ mg_status qs_plastic_work_grad(mg_ctx *ctx, qs_state *state, int nsteps, double 
         CK(cudaStreamSynchronize(ctx->st));
         W += wscale * ctx->hsum[0];
     }
-    // reverse, one segment at a time from its checkpoint
+    *work = W;
+    return MG_OK;
+}
+
+// reverse sweep over the checkpoints written by work_forward: each segment's
+// states are recomputed from its checkpoint (bitwise those of the forward
+// run: its time from t0 by the same sequence of additions), then the step
+// adjoints run backwards through them
+mg_status work_backward(mg_ctx *ctx, const double *cp, double t0, long step0, int nsteps,
+                        double dt, double tol, int seg, double *chibar, mg_stats *stats) {
+    const Dims &d = ctx->L[0];
+    const size_t nc = (size_t)d.nx * d.ny * d.nz, nv = corner_count(d);
+    const int ncp = (nsteps + seg - 1) / seg;
+    StateStore store;
+    std::vector<qs_state> ss(seg);
+    for (int c = 0; c < seg; c++) {
+        qs_state &q = ss[c];
+        q.v = store.get(nv);
+        q.sigma = store.get(6 * nc);
+        q.chi = store.get(nc);
+        if (!q.v || !q.sigma || !q.chi) {
+            set_err("qs_plastic_work_backward: out of device memory for %d segment states", seg);
+            return MG_ERR_OOM;
+        }
+    }
+    double *vbar = store.get(nv), *sigbar = store.get(6 * nc);
+    if (!vbar || !sigbar) {
+        set_err("qs_plastic_work_backward: out of device memory");
+        return MG_ERR_OOM;
+    }
+    // the times of the checkpoints, as the forward steps advanced them
+    std::vector<double> tcp(ncp);
+    double t = t0;
+    for (int n = 0; n < nsteps; n++) {
+        if (n % seg == 0) tcp[n / seg] = t;
+        t += dt;
+    }
     CK(cudaMemsetAsync(vbar, 0, nv * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(sigbar, 0, 6 * nc * sizeof(double), ctx->st));
     CK(cudaMemsetAsync(chibar, 0, nc * sizeof(double), ctx->st));
     for (int c = ncp - 1; c >= 0; c--) {
         const int n0 = c * seg, n1 = n0 + seg < nsteps ? n0 + seg : nsteps;
-        CK(copy_state(cp[c], ss[0]));
+        qs_state q = checkpoint_view(ctx, cp, c);
+        q.t = tcp[c];
+        q.step = step0 + n0;
+        CK(copy_state(ctx, q, ss[0]));
         for (int n = n0; n + 1 < n1; n++) {
-            CK(copy_state(ss[n - n0], ss[n - n0 + 1]));
+            CK(copy_state(ctx, ss[n - n0], ss[n - n0 + 1]));
             const mg_status s = qs_step(ctx, &ss[n - n0 + 1], dt, tol, nullptr);
             if (s != MG_OK) return s;
         }
@@ -1309,8 +1428,55 @@ mg_status qs_plastic_work_grad(mg_ctx *ctx, qs_state *state, int nsteps, double 
         }
     }
     CK(cudaStreamSynchronize(ctx->st));
-    *work = W;
     return MG_OK;
+}
+
+}  // namespace
+
+mg_status qs_plastic_work(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
+                          int checkpoint_every, double *checkpoints, double *work,
+                          mg_stats *stats) {
+    CKS(work_args(ctx, state, nsteps, dt, checkpoint_every, "qs_plastic_work"));
+    if (!state->v || !state->sigma || !state->chi || !work) {
+        set_err("qs_plastic_work: null array");
+        return MG_ERR_ARG;
+    }
+    const int seg = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+    return work_forward(ctx, state, nsteps, dt, tol, seg, checkpoints, work, stats);
+}
+
+mg_status qs_plastic_work_backward(mg_ctx *ctx, const double *checkpoints, double t0, long step0,
+                                   int nsteps, double dt, double tol, int checkpoint_every,
+                                   double *chibar, mg_stats *stats) {
+    CKS(work_args(ctx, checkpoints, nsteps, dt, checkpoint_every, "qs_plastic_work_backward"));
+    if (!chibar) {
+        set_err("qs_plastic_work_backward: null chibar");
+        return MG_ERR_ARG;
+    }
+    const int seg = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+    return work_backward(ctx, checkpoints, t0, step0, nsteps, dt, tol, seg, chibar, stats);
+}
+
+mg_status qs_plastic_work_grad(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
+                               int checkpoint_every, double *chibar, double *work,
+                               mg_stats *stats) {
+    CKS(work_args(ctx, state, nsteps, dt, checkpoint_every, "qs_plastic_work_grad"));
+    if (!state->v || !state->sigma || !state->chi || !chibar || !work) {
+        set_err("qs_plastic_work_grad: null array");
+        return MG_ERR_ARG;
+    }
+    const int seg = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+    const int ncp = (nsteps + seg - 1) / seg;
+    StateStore store;
+    double *cp = store.get((size_t)ncp * state_doubles(ctx->L[0]));
+    if (!cp) {
+        set_err("qs_plastic_work_grad: out of device memory for %d checkpoints", ncp);
+        return MG_ERR_OOM;
+    }
+    const double t0 = state->t;
+    const long step0 = state->step;
+    CKS(work_forward(ctx, state, nsteps, dt, tol, seg, cp, work, stats));
+    return work_backward(ctx, cp, t0, step0, nsteps, dt, tol, seg, chibar, stats);
 }
 
 // ------------------------------------------------------------ measurement

@@ -40,14 +40,76 @@ struct Fine {
     T d0, lp, kq, dinv;
 };
 
-// Coarse-level operator: one constant 27-point stencil of 3x3 blocks
-// (Galerkin product, Eq. 36) plus the inverse of its centre block.
-// Passed to kernels by value (lives in the kernel-parameter constant bank).
+// Coarse-level operator: one constant 27-point stencil of 3x3 blocks per
+// level (Galerkin product, Eq. 36).  Reflecting one axis maps the elastic
+// problem onto itself with that velocity component negated, and trilinear
+// interpolation commutes with the reflection, so every level keeps the
+// parity structure of the finest operator and is stored by parity class:
+//   A(d)_aa = cd[a][|dx| + 2|dy| + 4|dz|]       (cd[a][0]: the centre),
+//   A(d)_ab = s(d_a) s(d_b) g[c][|d_c|]          (a != b, c = 3 - a - b),
+// with s() the sign of an offset; A(d)_ab = 0 when d_a or d_b is 0, so the
+// centre block is diagonal and dinv[a] = 1 / cd[a][0].  Set-up checks the
+// table of every level against this form.  Passed to kernels by value (it
+// lives in the kernel-parameter constant bank).
 template <typename T>
 struct Coarse {
-    T S[243];
-    T Dinv[9];
+    T cd[3][8];
+    T g[3][2];
+    T dinv[3];
 };
+
+// sum over the 8 in-plane offsets (dz = 0) of A(d) u(p + d) for one node:
+// u(b, dx, dy) is component b of the neighbour at in-plane offset (dx, dy)
+template <typename T, class U>
+__host__ __device__ __forceinline__ void coarse_plane_terms(const Coarse<T> &c, const U &u,
+                                                            T o[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        o[a] = c.cd[a][1] * (u(a, -1, 0) + u(a, 1, 0)) + c.cd[a][2] * (u(a, 0, -1) + u(a, 0, 1)) +
+               c.cd[a][3] * ((u(a, -1, -1) + u(a, 1, 1)) + (u(a, 1, -1) + u(a, -1, 1)));
+    // the (x, y) coupling, |dz| = 0: sum of s(dx) s(dy) u_b
+    const T qy = (u(1, 1, 1) - u(1, 1, -1)) - (u(1, -1, 1) - u(1, -1, -1));
+    const T qx = (u(0, 1, 1) - u(0, 1, -1)) - (u(0, -1, 1) - u(0, -1, -1));
+    o[0] += c.g[2][0] * qy;
+    o[1] += c.g[2][0] * qx;
+}
+
+// sum over the 18 offsets with dz = +-1 of A(d) u(p + d) for one node, from
+// the sums S_b = u_b(dz = +1) + u_b(dz = -1) and differences
+// D_b = u_b(+1) - u_b(-1) at the 9 in-plane positions: sd(b, dx, dy, S, D)
+// fills S and D of component b at in-plane offset (dx, dy)
+template <typename T, class SD>
+__host__ __device__ __forceinline__ void coarse_z_terms(const Coarse<T> &c, const SD &sd,
+                                                        T o[3]) {
+    T S[3][3][3], D[3][3][3];  // [b][dy + 1][dx + 1]
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 1; dx++) sd(b, dx, dy, S[b][dy + 1][dx + 1], D[b][dy + 1][dx + 1]);
+    T add[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        add[a] = c.cd[a][4] * S[a][1][1] + c.cd[a][5] * (S[a][1][0] + S[a][1][2]) +
+                 c.cd[a][6] * (S[a][0][1] + S[a][2][1]) +
+                 c.cd[a][7] * ((S[a][0][0] + S[a][2][2]) + (S[a][0][2] + S[a][2][0]));
+    // (x, y), third axis z, |dz| = 1: s(dx) s(dy) over S
+    add[0] += c.g[2][1] * ((S[1][2][2] - S[1][0][2]) - (S[1][2][0] - S[1][0][0]));
+    add[1] += c.g[2][1] * ((S[0][2][2] - S[0][0][2]) - (S[0][2][0] - S[0][0][0]));
+    // (x, z), third axis y: s(dx) s(dz) g[1][|dy|], the dz sum giving D
+    add[0] += c.g[1][0] * (D[2][1][2] - D[2][1][0]) +
+              c.g[1][1] * ((D[2][0][2] - D[2][0][0]) + (D[2][2][2] - D[2][2][0]));
+    add[2] += c.g[1][0] * (D[0][1][2] - D[0][1][0]) +
+              c.g[1][1] * ((D[0][0][2] - D[0][0][0]) + (D[0][2][2] - D[0][2][0]));
+    // (y, z), third axis x: s(dy) s(dz) g[0][|dx|]
+    add[1] += c.g[0][0] * (D[2][2][1] - D[2][0][1]) +
+              c.g[0][1] * ((D[2][2][0] - D[2][0][0]) + (D[2][2][2] - D[2][0][2]));
+    add[2] += c.g[0][0] * (D[1][2][1] - D[1][0][1]) +
+              c.g[0][1] * ((D[1][2][0] - D[1][0][0]) + (D[1][2][2] - D[1][0][2]));
+#pragma unroll
+    for (int a = 0; a < 3; a++) o[a] += add[a];
+}
 
 // fixed reduction geometry: partial sums per block, then one block adds them
 // in a fixed order, so every norm is bitwise reproducible
@@ -78,16 +140,31 @@ cudaError_t residual_fine_rows(const Dims &d, const Fine<float> &f, const float 
 bool coarse_rows_fit(const Dims &d);
 cudaError_t gs_sweep_coarse_rows(const Dims &d, const Coarse<float> &c, const float *b,
                                  const float *vin, float *vout, bool descending, cudaStream_t s);
-// FP32 finest-level sweep vin -> vout with the row-strip kernels;
-// cudaErrorNotSupported when the rows are too long for them
+// Cross-CTA state of the fused finest-level sweep (device memory, zeroed at
+// allocation, owned by the context): per-tile ready flags that hold the
+// launch count + 1 once the tile is done, the exchange rows of each chunk's
+// lead-in tile, the launch count, and an error word set when a bounded wait
+// gives up.  Sized by fused_sweep_sizes.
+struct SweepSync {
+    int *aflag;   // [nstrips][nsteps + 1]
+    int *pflag;   // [nchunks]
+    float *xbuf;  // [nchunks][6 strip rows][3][nx]
+    int *epoch, *done, *err;
+};
+// whether the fused sweep takes this grid, and the sizes of its SweepSync
+// arrays (in elements); false if it does not apply
+bool fused_sweep_sizes(const Dims &d, long &naflag, long &npflag, long &nxbuf);
+// FP32 finest-level sweep vin -> vout with the row-strip kernels: the fused
+// one-launch sweep when sync is given and the grid suits it, else the two
+// phase launches; cudaErrorNotSupported when the rows are too long for them
 cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
                                const float *vin, float *vout, bool descending, cudaStream_t s,
-                               int split);
+                               int split, const SweepSync *sync = nullptr);
 // tiled FP32 finest-level sweep vin -> vout (two phase launches); split:
 // the arrays are in parity-split column order
 cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,
                                 const float *vin, float *vout, bool descending, cudaStream_t s,
-                                int split = 0);
+                                int split = 0, const SweepSync *sync = nullptr);
 
 // tiled FP32 coarse-level sweep vin -> vout (27-point block stencil)
 cudaError_t gs_sweep_coarse_tiled(const Dims &d, const Coarse<float> &c, const float *b,

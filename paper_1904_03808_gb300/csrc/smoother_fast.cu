@@ -117,50 +117,32 @@ struct FineOp {
     }
 };
 
-// coarse levels: one constant 27-point stencil of 3x3 blocks (Eq. 36)
+// coarse levels: one constant 27-point stencil of 3x3 blocks (Eq. 36), in
+// parity-class form
 template <typename T>
 struct CoarseOp {
     static constexpr bool kStageZ = false;
     Coarse<T> c;
     __device__ __forceinline__ void update(const View<T> &v, int wx, int wy) const {
-        T s0 = 0, s1 = 0, s2 = 0;
-#pragma unroll
-        for (int dz = -1; dz <= 1; dz++)
-#pragma unroll
-            for (int dy = -1; dy <= 1; dy++)
-#pragma unroll
-                for (int dx = -1; dx <= 1; dx++) {
-                    const int dd = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-                    if (dd == 13) continue;
-                    T u0, u1, u2;
-                    if (dz == 0) {
-                        u0 = v.P[widx(0, wy + dy, wx + dx)];
-                        u1 = v.P[widx(1, wy + dy, wx + dx)];
-                        u2 = v.P[widx(2, wy + dy, wx + dx)];
-                    } else {
-                        const T *Z = dz < 0 ? v.L : v.H;
-                        const int g = v.rowg[wy + dy] + v.colg[wx + dx];
-                        u0 = __ldg(Z + g);
-                        u1 = __ldg(Z + v.cs + g);
-                        u2 = __ldg(Z + 2 * v.cs + g);
-                    }
-                    const T *S = c.S + dd * 9;
-                    s0 += S[0] * u0 + S[1] * u1 + S[2] * u2;
-                    s1 += S[3] * u0 + S[4] * u1 + S[5] * u2;
-                    s2 += S[6] * u0 + S[7] * u1 + S[8] * u2;
-                }
+        T o[3];
+        auto u = [&](int b, int dx, int dy) -> T { return v.P[widx(b, wy + dy, wx + dx)]; };
+        auto sd = [&](int b, int dx, int dy, T &S, T &D) {
+            const int g = v.rowg[wy + dy] + v.colg[wx + dx];
+            const T lo = __ldg(v.L + b * v.cs + g), hi = __ldg(v.H + b * v.cs + g);
+            S = hi + lo;
+            D = hi - lo;
+        };
+        coarse_plane_terms(c, u, o);
+        coarse_z_terms(c, sd, o);
         const int g00 = v.rowg[wy] + v.colg[wx];
-        const T f0 = __ldg(v.B + g00) - s0, f1 = __ldg(v.B + v.cs + g00) - s1,
-                f2 = __ldg(v.B + 2 * v.cs + g00) - s2;
-        v.P[widx(0, wy, wx)] = c.Dinv[0] * f0 + c.Dinv[1] * f1 + c.Dinv[2] * f2;
-        v.P[widx(1, wy, wx)] = c.Dinv[3] * f0 + c.Dinv[4] * f1 + c.Dinv[5] * f2;
-        v.P[widx(2, wy, wx)] = c.Dinv[6] * f0 + c.Dinv[7] * f1 + c.Dinv[8] * f2;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            v.P[widx(a, wy, wx)] = c.dinv[a] * (__ldg(v.B + a * v.cs + g00) - o[a]);
     }
 };
 
 // resident CTAs per SM the register budget is cut for: the 27-point operator
-// keeps its 243 coefficients in registers (~128 registers a thread in FP32);
-// the 19-point one needs about 40
+// needs more registers a thread than the 19-point one
 template <class Op>
 struct MinBlocks {
     static constexpr int value = 6;
@@ -398,30 +380,18 @@ __global__ void __launch_bounds__(kPlaneThreads)
     // fold the z-neighbour blocks (dz = -1, +1) into the right-hand side
     for (int m = threadIdx.x; m < np; m += blockDim.x) {
         const int j = m / nx, i = m - j * nx;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int dz = -1; dz <= 1; dz += 2) {
-            const float *Z = dz < 0 ? Lz : Hz;
-#pragma unroll
-            for (int dy = -1; dy <= 1; dy++) {
-                int jj = j + dy;
-                jj = jj < 0 ? jj + ny : (jj >= ny ? jj - ny : jj);
-#pragma unroll
-                for (int dx = -1; dx <= 1; dx++) {
-                    int ii = i + dx;
-                    ii = ii < 0 ? ii + nx : (ii >= nx ? ii - nx : ii);
-                    const int q = jj * nx + ii;
-                    const float u0 = Z[q], u1 = Z[np + q], u2 = Z[2 * np + q];
-                    const float *S = c.S + ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) * 9;
-                    s0 += S[0] * u0 + S[1] * u1 + S[2] * u2;
-                    s1 += S[3] * u0 + S[4] * u1 + S[5] * u2;
-                    s2 += S[6] * u0 + S[7] * u1 + S[8] * u2;
-                }
-            }
-        }
-        Rr[m] -= s0;
-        Rr[np + m] -= s1;
-        Rr[2 * np + m] -= s2;
+        const int col[3] = {i ? i - 1 : nx - 1, i, i + 1 < nx ? i + 1 : 0};
+        const int row[3] = {(j ? j - 1 : ny - 1) * nx, j * nx, (j + 1 < ny ? j + 1 : 0) * nx};
+        auto sd = [&](int b, int dx, int dy, float &S, float &D) {
+            const int q = b * np + row[dy + 1] + col[dx + 1];
+            S = Hz[q] + Lz[q];
+            D = Hz[q] - Lz[q];
+        };
+        float o[3] = {0.f, 0.f, 0.f};
+        coarse_z_terms(c, sd, o);
+        Rr[m] -= o[0];
+        Rr[np + m] -= o[1];
+        Rr[2 * np + m] -= o[2];
     }
     __syncthreads();
     // colours (F,F), (1-F,F), (F,1-F), (1-F,1-F) in (x, y) parity
@@ -431,29 +401,16 @@ __global__ void __launch_bounds__(kPlaneThreads)
         const int pi = (pass & 1) ? 1 - F : F, pj = (pass & 2) ? 1 - F : F;
         for (int t = threadIdx.x; t < nh; t += blockDim.x) {
             const int jh = t / hx, i = 2 * (t - jh * hx) + pi, j = 2 * jh + pj;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-            for (int dy = -1; dy <= 1; dy++) {
-                int jj = j + dy;
-                jj = jj < 0 ? jj + ny : (jj >= ny ? jj - ny : jj);
-#pragma unroll
-                for (int dx = -1; dx <= 1; dx++) {
-                    if (dy == 0 && dx == 0) continue;
-                    int ii = i + dx;
-                    ii = ii < 0 ? ii + nx : (ii >= nx ? ii - nx : ii);
-                    const int q = jj * nx + ii;
-                    const float u0 = P[q], u1 = P[np + q], u2 = P[2 * np + q];
-                    const float *S = c.S + (9 + (dy + 1) * 3 + (dx + 1)) * 9;
-                    s0 += S[0] * u0 + S[1] * u1 + S[2] * u2;
-                    s1 += S[3] * u0 + S[4] * u1 + S[5] * u2;
-                    s2 += S[6] * u0 + S[7] * u1 + S[8] * u2;
-                }
-            }
+            const int col[3] = {i ? i - 1 : nx - 1, i, i + 1 < nx ? i + 1 : 0};
+            const int row[3] = {(j ? j - 1 : ny - 1) * nx, j * nx, (j + 1 < ny ? j + 1 : 0) * nx};
+            auto u = [&](int b, int dx, int dy) -> float {
+                return P[b * np + row[dy + 1] + col[dx + 1]];
+            };
+            float o[3];
+            coarse_plane_terms(c, u, o);
             const int m = j * nx + i;
-            const float f0 = Rr[m] - s0, f1 = Rr[np + m] - s1, f2 = Rr[2 * np + m] - s2;
-            P[m] = c.Dinv[0] * f0 + c.Dinv[1] * f1 + c.Dinv[2] * f2;
-            P[np + m] = c.Dinv[3] * f0 + c.Dinv[4] * f1 + c.Dinv[5] * f2;
-            P[2 * np + m] = c.Dinv[6] * f0 + c.Dinv[7] * f1 + c.Dinv[8] * f2;
+#pragma unroll
+            for (int a = 0; a < 3; a++) P[a * np + m] = c.dinv[a] * (Rr[a * np + m] - o[a]);
         }
         __syncthreads();
     }
@@ -490,9 +447,9 @@ cudaError_t plane_init() {
 // one 8-colour sweep vin -> vout (vout's wall planes must hold the walls)
 cudaError_t gs_sweep_fine_tiled(const Dims &d, const Fine<float> &f, const float *b,
                                 const float *vin, float *vout, bool descending, cudaStream_t s,
-                                int split) {
+                                int split, const SweepSync *sync) {
     // whole rows per CTA where the rows are short enough (smoother_rows.cu)
-    const cudaError_t e = gs_sweep_fine_rows(d, f, b, vin, vout, descending, s, split);
+    const cudaError_t e = gs_sweep_fine_rows(d, f, b, vin, vout, descending, s, split, sync);
     if (e != cudaErrorNotSupported) return e;
     FineOp<float> op{f};
     return sweep<float>(d, op, b, vin, vout, descending, s, split);

@@ -349,11 +349,20 @@ struct FineRowsOp {
     template <int R>
     __device__ __forceinline__ void fold(float (&r)[3][2][R], const float *Ls, const float *Hs,
                                          const float *Bs, const RowCols &q) const {
+        auto bv = [&](int jj, int c, int e) { return Bs[q.at(jj - 1, c, e ? q.xo : q.xe)]; };
+        fold_with<R>(r, Ls, Hs, bv, q);
+    }
+    // the same with the right-hand side of window row jj, component c, node
+    // e (0: E, 1: O) given by bv(jj, c, e)
+    template <int R, class BV_>
+    __device__ __forceinline__ void fold_with(float (&r)[3][2][R], const float *Ls,
+                                              const float *Hs, const BV_ &bv,
+                                              const RowCols &q) const {
         const float lp = f.lp, kq = f.kq;
         const int xe = q.xe, xo = q.xo, xom = q.xom, xep = q.xep;
 #define DZ(row, c, x) (Hs[q.at(row, c, x)] - Ls[q.at(row, c, x)])
 #define SZ(row, c, x) (Hs[q.at(row, c, x)] + Ls[q.at(row, c, x)])
-#define BV(c, x) Bs[q.at(jj - 1, c, x)]
+#define BV(c, e) bv(jj, c, e)
 #pragma unroll
         for (int jj = 1; jj < R - 1; jj++) {
             const float dOm0 = DZ(jj, 0, xom), dOm2 = DZ(jj, 2, xom);
@@ -361,16 +370,16 @@ struct FineRowsOp {
             const float dE0 = DZ(jj, 0, xe), dE2 = DZ(jj, 2, xe);
             const float dO0 = DZ(jj, 0, xo), dO2 = DZ(jj, 2, xo);
             // E node: x-1 is the neighbour's O column, x+1 the own O column
-            r[0][0][jj] = BV(0, xe) + (SZ(jj, 0, xe) + kq * (dO2 - dOm2));
+            r[0][0][jj] = BV(0, 0) + (SZ(jj, 0, xe) + kq * (dO2 - dOm2));
             r[1][0][jj] =
-                BV(1, xe) + (SZ(jj, 1, xe) + kq * (DZ(jj + 1, 2, xe) - DZ(jj - 1, 2, xe)));
-            r[2][0][jj] = BV(2, xe) + (lp * SZ(jj, 2, xe) +
+                BV(1, 0) + (SZ(jj, 1, xe) + kq * (DZ(jj + 1, 2, xe) - DZ(jj - 1, 2, xe)));
+            r[2][0][jj] = BV(2, 0) + (lp * SZ(jj, 2, xe) +
                                        kq * ((dO0 - dOm0) + (DZ(jj + 1, 1, xe) - DZ(jj - 1, 1, xe))));
             // O node: x-1 is the own E column, x+1 the neighbour's E column
-            r[0][1][jj] = BV(0, xo) + (SZ(jj, 0, xo) + kq * (dEp2 - dE2));
+            r[0][1][jj] = BV(0, 1) + (SZ(jj, 0, xo) + kq * (dEp2 - dE2));
             r[1][1][jj] =
-                BV(1, xo) + (SZ(jj, 1, xo) + kq * (DZ(jj + 1, 2, xo) - DZ(jj - 1, 2, xo)));
-            r[2][1][jj] = BV(2, xo) + (lp * SZ(jj, 2, xo) +
+                BV(1, 1) + (SZ(jj, 1, xo) + kq * (DZ(jj + 1, 2, xo) - DZ(jj - 1, 2, xo)));
+            r[2][1][jj] = BV(2, 1) + (lp * SZ(jj, 2, xo) +
                                        kq * ((dEp0 - dE0) + (DZ(jj + 1, 1, xo) - DZ(jj - 1, 1, xo))));
         }
 #undef DZ
@@ -413,34 +422,33 @@ struct CoarseRowsOp {
         const int xl = q.xom - 1, xr = q.xep;  // first columns of the left / right pairs
 #pragma unroll
         for (int jj = 1; jj < R - 1; jj++) {
-            float sE[3] = {0.f, 0.f, 0.f}, sO[3] = {0.f, 0.f, 0.f};
+            // z sums and differences at columns x_E - 1, x_E, x_O, x_O + 1
+            float S[3][3][4], D[3][3][4];  // [component][dy + 1][column]
 #pragma unroll
-            for (int dz = -1; dz <= 1; dz += 2) {
-                const float *Z = dz < 0 ? Ls : Hs;
+            for (int b = 0; b < 3; b++)
 #pragma unroll
-                for (int dy = -1; dy <= 1; dy++)
+                for (int dy = -1; dy <= 1; dy++) {
+                    const float2 ll = pair(Ls, q, jj + dy, b, xl), lo = pair(Ls, q, jj + dy, b, q.xe),
+                                 lr = pair(Ls, q, jj + dy, b, xr);
+                    const float2 hl = pair(Hs, q, jj + dy, b, xl), ho = pair(Hs, q, jj + dy, b, q.xe),
+                                 hr = pair(Hs, q, jj + dy, b, xr);
+                    const float L4[4] = {ll.y, lo.x, lo.y, lr.x}, H4[4] = {hl.y, ho.x, ho.y, hr.x};
 #pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        const float2 lft = pair(Z, q, jj + dy, d, xl);
-                        const float2 own = pair(Z, q, jj + dy, d, q.xe);
-                        const float2 rgt = pair(Z, q, jj + dy, d, xr);
-                        const float uE[3] = {lft.y, own.x, own.y}, uO[3] = {own.x, own.y, rgt.x};
-#pragma unroll
-                        for (int dx = 0; dx < 3; dx++) {
-                            const float *S = c.S + ((dz + 1) * 9 + (dy + 1) * 3 + dx) * 9 + d;
-#pragma unroll
-                            for (int a = 0; a < 3; a++) {
-                                sE[a] += S[3 * a] * uE[dx];
-                                sO[a] += S[3 * a] * uO[dx];
-                            }
-                        }
+                    for (int m = 0; m < 4; m++) {
+                        S[b][dy + 1][m] = H4[m] + L4[m];
+                        D[b][dy + 1][m] = H4[m] - L4[m];
                     }
-            }
+                }
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const float2 bb = pair(Bs, q, jj - 1, a, q.xe);
-                r[a][0][jj] = bb.x - sE[a];
-                r[a][1][jj] = bb.y - sO[a];
+            for (int e = 0; e < 2; e++) {
+                auto sd = [&](int b, int dx, int dy, float &s_, float &d_) {
+                    s_ = S[b][dy + 1][e + dx + 1];
+                    d_ = D[b][dy + 1][e + dx + 1];
+                };
+                float o[3] = {0.f, 0.f, 0.f};
+                coarse_z_terms(c, sd, o);
+#pragma unroll
+                for (int a = 0; a < 3; a++) r[a][e][jj] = Bs[q.at(jj - 1, a, e ? q.xo : q.xe)] - o[a];
             }
         }
     }
@@ -448,44 +456,34 @@ struct CoarseRowsOp {
     __device__ __forceinline__ void numer(const float (&P)[3][2][R], const float (&r)[3][2][R],
                                           const float *X, const RowCols &q, int jj,
                                           float num[3]) const {
-        float s[3] = {0.f, 0.f, 0.f};
         const int xfar = E == 0 ? q.xom - 1 : q.xep;  // the far-side neighbour's pair
+        float far[3][3];                              // [component][dy + 1]
 #pragma unroll
-        for (int dy = -1; dy <= 1; dy++) {
-            float far[3];
+        for (int dy = -1; dy <= 1; dy++)
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const float2 p2 = pair(X, q, jj + dy, d, xfar);
-                far[d] = E == 0 ? p2.y : p2.x;
+            for (int b = 0; b < 3; b++) {
+                const float2 p2 = pair(X, q, jj + dy, b, xfar);
+                far[b][dy + 1] = E == 0 ? p2.y : p2.x;
             }
+        // x - 1 of E / x + 1 of O: the far-side column; otherwise the own E
+        // (offset 0 of E, -1 of O) or the own O column
+        auto u = [&](int b, int dx, int dy) -> float {
+            if (E == 0 ? dx < 0 : dx > 0) return far[b][dy + 1];
+            const int own = E == 0 ? (dx == 0 ? 0 : 1) : (dx == 0 ? 1 : 0);
+            return P[b][own][jj + dy];
+        };
+        float o[3];
+        coarse_plane_terms(c, u, o);
 #pragma unroll
-            for (int dx = -1; dx <= 1; dx++) {
-                if (dy == 0 && dx == 0) continue;
-                // x - 1 of E / x + 1 of O: the far-side column; otherwise the
-                // own E (offset 0 of E, -1 of O) or the own O column
-                const bool isfar = E == 0 ? dx < 0 : dx > 0;
-                const int own = E == 0 ? (dx == 0 ? 0 : 1) : (dx == 0 ? 1 : 0);
-                const float *S = c.S + (9 + (dy + 1) * 3 + (dx + 1)) * 9;
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    const float u = isfar ? far[d] : P[d][own][jj + dy];
-#pragma unroll
-                    for (int a = 0; a < 3; a++) s[a] += S[3 * a + d] * u;
-                }
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 3; a++) num[a] = r[a][E][jj] - s[a];
+        for (int a = 0; a < 3; a++) num[a] = r[a][E][jj] - o[a];
     }
     __device__ __forceinline__ void solve(const float num[3], float out[3]) const {
 #pragma unroll
-        for (int a = 0; a < 3; a++)
-            out[a] = c.Dinv[3 * a] * num[0] + c.Dinv[3 * a + 1] * num[1] + c.Dinv[3 * a + 2] * num[2];
+        for (int a = 0; a < 3; a++) out[a] = c.dinv[a] * num[a];
     }
     __device__ __forceinline__ void centre(const float x[3], float out[3]) const {
-        const float *S = c.S + 13 * 9;
 #pragma unroll
-        for (int a = 0; a < 3; a++) out[a] = S[3 * a] * x[0] + S[3 * a + 1] * x[1] + S[3 * a + 2] * x[2];
+        for (int a = 0; a < 3; a++) out[a] = c.cd[a][0] * x[a];
     }
 };
 
@@ -732,6 +730,375 @@ cudaError_t rows_p_sweep(const Dims &d, const OP &op, const float *b, const floa
     return launch_rows_p<OP, 1, SPLIT, false>(d, op, b, vin, vout, vout, 2, 2, ne, s, sms);
 }
 
+// ------------------------------------------------------------------------
+// Fused sweep: both phases of an 8-colour sweep in one launch, so that v is
+// read from DRAM once per sweep instead of once per phase.  The planes of the
+// first phase ("A": the even planes, colours 0-3, in an ascending sweep; the
+// odd ones, colours 7-4, in a descending sweep) depend only on the sweep's
+// input; a plane of the second phase ("B") needs the new values of the A
+// planes just below and above it.  Each CTA owns one row strip of TY rows
+// and a contiguous run of "steps" along z; step m updates A plane
+// kA(m) = kA0 + 2 (m - 1) and then B plane kA(m) - 1, whose z-neighbours
+// are the A planes of steps m - 1 and m, both still in shared memory.  The
+// window rows of a new A plane outside the strip come from the neighbouring
+// strips' CTAs: each publishes a ready flag per (strip, step) after storing
+// its tile, and a CTA waits for the flags of the rows it needs before it
+// copies them (from L2: they were just written).  A run that does not start
+// at step 1 first recomputes the A plane of the step before it (exactly as
+// the run below computes it) and exchanges that tile's boundary rows with
+// its neighbours through a small buffer, so runs along z never wait on each
+// other.  All CTAs are co-resident (cooperative launch); every wait is
+// bounded and sets the error word when it gives up (the sweep then carries
+// on with whatever it read, and the host reports the error).
+//
+// Shared memory: four windows of R rows x 3 components x nx (110.6 KB at
+// nx = 256, two CTAs per SM): the A plane being updated, the new A plane of
+// the previous step, the old B plane of this step (updated in place by the
+// second phase) and the old B plane above the A plane.  Right-hand-side rows
+// are loaded from global memory into registers.
+
+constexpr long kSpinMax = 1L << 22;  // flag polls before a wait gives up (about 2 s)
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+// wait until *f >= want, polling at most kSpinMax times; on giving up (or if
+// another wait already gave up) set / leave the error word and return
+__device__ __forceinline__ void wait_flag(const int *f, int want, int *err) {
+    for (long it = 0; it < kSpinMax; it++) {
+        if (ld_acquire(f) >= want) return;
+        if (*(volatile int *)err) return;
+        __nanosleep(64);
+    }
+    atomicOr(err, 1);
+}
+
+constexpr int kFusedWindows = 4;
+__host__ __device__ constexpr long fused_floats(int nx) {
+    return (long)kFusedWindows * 3 * kPersR * nx;
+}
+
+// one tile update of plane k (window Wk, in place) with z-neighbour windows
+// WL, WH and right-hand side bb; after_fold runs once every thread has
+// folded (WL and WH are then free); the final tile values are left in Wk
+// (every pass writes its nodes there) and, if store, in plane k of vout
+template <int F, bool SPLIT, class AF>
+__device__ __forceinline__ void fused_tile(const FineRowsOp &op, float *Wk, const float *WL,
+                                           const float *WH, const float (&bb)[3][2][kPersR],
+                                           const RowCols &q, float *vout, long ps, long cs,
+                                           int k, int y0, int ny, bool store, const AF &after_fold) {
+    constexpr int TY = kPersTY, R = kPersR;
+    float r[3][2][R];
+    auto bv = [&](int jj, int c, int e) { return bb[c][e][jj]; };
+    op.template fold_with<R>(r, WL, WH, bv, q);
+    float P[3][2][R];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int jj = 0; jj < R; jj++) {
+            P[c][0][jj] = Wk[q.at(jj, c, q.xe)];
+            P[c][1][jj] = Wk[q.at(jj, c, q.xo)];
+        }
+    __syncthreads();
+    after_fold();
+    constexpr int EF = F, EG = 1 - F;
+    const int xF = EF == 0 ? q.xe : q.xo, xG = EG == 0 ? q.xe : q.xo;
+    // pass 1: x-parity F on the odd rows
+#pragma unroll
+    for (int jj = 1; jj < R - 1; jj += 2) {
+        pers_update<EF, R>(op, P, r, Wk, q, jj);
+#pragma unroll
+        for (int c = 0; c < 3; c++) Wk[q.at(jj, c, xF)] = P[c][EF][jj];
+    }
+    __syncthreads();
+    // pass 2: x-parity 1-F on the odd rows
+#pragma unroll
+    for (int jj = 1; jj < R - 1; jj += 2) {
+        pers_update<EG, R>(op, P, r, Wk, q, jj);
+#pragma unroll
+        for (int c = 0; c < 3; c++) Wk[q.at(jj, c, xG)] = P[c][EG][jj];
+    }
+    __syncthreads();
+    // pass 3: x-parity F on the even rows
+#pragma unroll
+    for (int jj = 2; jj < R - 2; jj += 2) {
+        pers_update<EF, R>(op, P, r, Wk, q, jj);
+#pragma unroll
+        for (int c = 0; c < 3; c++) Wk[q.at(jj, c, xF)] = P[c][EF][jj];
+    }
+    __syncthreads();
+    // pass 4: x-parity 1-F on the even rows (its readers read only the
+    // other parity's columns, so the results can go to Wk at once)
+#pragma unroll
+    for (int jj = 2; jj < R - 2; jj += 2) {
+        pers_update<EG, R>(op, P, r, Wk, q, jj);
+#pragma unroll
+        for (int c = 0; c < 3; c++) Wk[q.at(jj, c, xG)] = P[c][EG][jj];
+    }
+    if (store) {
+        float *Ok = vout + (long)k * ps;
+#pragma unroll
+        for (int jj = 1 + F; jj < TY + 1 + F; jj++) {
+            const int y = y0 - 1 - F + jj;
+            if (y < ny) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    Ok[c * cs + (long)y * q.nx + q.xe] = P[c][0][jj];
+                    Ok[c * cs + (long)y * q.nx + q.xo] = P[c][1][jj];
+                }
+            }
+        }
+    }
+}
+
+template <int F, bool SPLIT>
+__global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
+    k_gs_rows_f(Dims d, FineRowsOp op, const float *__restrict__ b, const float *__restrict__ vin,
+                float *__restrict__ vout, int kA0, int nsteps, int nstrips, int kz, SweepSync sy) {
+    constexpr int TY = kPersTY, R = kPersR;
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int s_epoch;
+    const int nx = d.nx, ny = d.ny, nz = d.nz, hn = nx >> 1, cpr = nx >> 2;
+    const long ps = (long)nx * ny, cs = d.cs;
+    const int win = 3 * R * nx;
+    const int t = threadIdx.x;
+    const int q4 = 4 * (t % cpr), g = t / cpr;
+    const int tm = t == 0 ? hn - 1 : t - 1, tp = t + 1 == hn ? 0 : t + 1;
+    RowCols q;
+    q.nx = nx;
+    q.xe = SPLIT ? t : 2 * t;
+    q.xo = SPLIT ? hn + t : 2 * t + 1;
+    q.xom = SPLIT ? hn + tm : 2 * tm + 1;
+    q.xep = SPLIT ? tp : 2 * tp;
+    const int chunk = blockIdx.x, s = chunk % nstrips, zc = chunk / nstrips;
+    const int m0 = 1 + (int)((long)zc * nsteps / kz), m1 = 1 + (int)((long)(zc + 1) * nsteps / kz);
+    const int y0 = s * TY, slen = ny - y0 < TY ? ny - y0 : TY;
+    if (t == 0) s_epoch = *(volatile int *)sy.epoch;
+    __syncthreads();
+    const int want = s_epoch + 1;
+    // window slot i (its role changes from step to step)
+    auto W = [&](int i) { return sm + i * win; };
+    int iAp = 0, iA = 1, iBc = 2, iBn = 3;
+
+    // grid row of window row jj (wrapped) and whether it lies outside the strip
+    auto wrow = [&](int jj) {
+        const int y = y0 - 1 - F + jj;
+        return y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    };
+    auto halo = [&](int jj) {
+        const int y = y0 - 1 - F + jj;
+        return y < y0 || y >= y0 + slen;
+    };
+    // window rows [jlo, jhi) of plane k of src into window dst
+    auto copy_rows = [&](float *dst, const float *src, int k, int jlo, int jhi) {
+        const float *base = src + (long)k * ps + q4;
+        for (int jj = jlo + g; jj < jhi; jj += 2) {
+            const float *srow = base + (long)wrow(jj) * nx;
+            float *drow = dst + jj * 3 * nx + q4;
+            cp_async16(drow, srow);
+            cp_async16(drow + nx, srow + cs);
+            cp_async16(drow + 2 * nx, srow + 2 * cs);
+        }
+    };
+    auto load_plane = [&](float *dst, int k) { copy_rows(dst, vin, k, 0, R); };
+    // right-hand side of window rows 1 .. R-2 of plane k into registers
+    auto load_b = [&](float (&bb)[3][2][R], int k) {
+        const float *Bk = b + (long)k * ps;
+#pragma unroll
+        for (int jj = 1; jj < R - 1; jj++) {
+            const long o = (long)wrow(jj) * nx;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                bb[c][0][jj] = __ldg(Bk + c * cs + o + q.xe);
+                bb[c][1][jj] = __ldg(Bk + c * cs + o + q.xo);
+            }
+        }
+    };
+    auto publish = [&](int *flag) {
+        __syncthreads();
+        if (t == 0) {
+            __threadfence();
+            st_release(flag, want);
+        }
+    };
+    // thread 0 waits for the flags of the owners of the window's halo rows
+    auto wait_owners = [&](const int *flags, long stride, long offset) {
+        if (t == 0) {
+            int last = -1;
+            for (int jj = 0; jj < R; jj++) {
+                if (!halo(jj)) continue;
+                const int o = wrow(jj) / TY;
+                if (o == last) continue;
+                last = o;
+                wait_flag(flags + o * stride + offset, want, sy.err);
+            }
+        }
+        __syncthreads();
+    };
+    const int nop = 0;
+    auto none = [&]() { (void)nop; };
+    float bb[3][2][R];  // right-hand side of the tile being updated
+
+    // ---- lead-in
+    const int kA1 = kA0 + 2 * (m0 - 1);  // A plane of the first step
+    if (m0 > 1) {
+        // recompute the A plane of step m0 - 1 (the run below computes and
+        // stores it); the window slot of this run's first A plane holds its
+        // lower neighbour meanwhile
+        const int kP = kA1 - 2;
+        load_plane(W(iAp), kP);
+        load_plane(W(iA), kP - 1);
+        load_plane(W(iBc), kP + 1);
+        cp_async_commit();
+        load_b(bb, kP);
+        cp_async_wait_all();
+        __syncthreads();
+        fused_tile<F, SPLIT>(op, W(iAp), W(iA), W(iBc), bb, q, vout, ps, cs, kP, y0, ny, false,
+                             none);
+        // its strip rows into the exchange buffer
+        float *xb = sy.xbuf + (long)chunk * TY * 3 * nx;
+        for (int rr = 0; rr < slen; rr++) {
+            const int jj = 1 + F + rr;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                xb[(rr * 3 + c) * nx + q.xe] = W(iAp)[q.at(jj, c, q.xe)];
+                xb[(rr * 3 + c) * nx + q.xo] = W(iAp)[q.at(jj, c, q.xo)];
+            }
+        }
+        publish(sy.pflag + chunk);
+        // this run's first A plane and the B plane above it
+        load_plane(W(iA), kA1);
+        if (kA1 + 1 <= nz) load_plane(W(iBn), kA1 + 1);
+        cp_async_commit();
+        // the lead-in plane's halo rows from the neighbours' exchange rows
+        wait_owners(sy.pflag, 1, (long)zc * nstrips);
+        for (int jj = 0; jj < R; jj++) {
+            if (!halo(jj)) continue;
+            const int y = wrow(jj), o = y / TY, rr = y - o * TY;
+            const float *src = sy.xbuf + ((long)(zc * nstrips + o) * TY + rr) * 3 * nx;
+            if (g == (jj & 1)) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) cp_async16(W(iAp) + (jj * 3 + c) * nx + q4, src + c * nx + q4);
+            }
+        }
+        cp_async_commit();
+    } else {
+        if (kA1 - 2 >= 0) load_plane(W(iAp), kA1 - 2);  // the wall below (ascending)
+        load_plane(W(iBc), kA1 - 1);
+        load_plane(W(iA), kA1);
+        if (kA1 + 1 <= nz) load_plane(W(iBn), kA1 + 1);
+        cp_async_commit();
+    }
+
+    // ---- the run's steps
+    for (int m = m0; m < m1; m++) {
+        const int kA = kA0 + 2 * (m - 1), kB = kA - 1;
+        const bool Aok = kA <= nz - 1, Bok = kB >= 1;
+        if (Aok) load_b(bb, kA);
+        cp_async_wait_all();
+        __syncthreads();
+        if (Aok) {
+            fused_tile<F, SPLIT>(op, W(iA), W(iBc), W(iBn), bb, q, vout, ps, cs, kA, y0, ny, true,
+                                 none);
+            // the B tile's right-hand side, in flight during the wait below
+            if (Bok) load_b(bb, kB);
+            publish(sy.aflag + (long)s * (nsteps + 1) + m);
+            // the new plane's window rows outside the strip, from the
+            // neighbours' stores
+            wait_owners(sy.aflag, nsteps + 1, m);
+            const float *Ok = vout + (long)kA * ps + q4;
+            for (int jj = g; jj < R; jj += 2) {
+                if (!halo(jj)) continue;
+                const float *srow = Ok + (long)wrow(jj) * nx;
+                float *drow = W(iA) + jj * 3 * nx + q4;
+                cp_async16(drow, srow);
+                cp_async16(drow + nx, srow + cs);
+                cp_async16(drow + 2 * nx, srow + 2 * cs);
+            }
+            cp_async_commit();
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        const bool more = m + 1 < m1;
+        // next step's A plane into the slot of the previous A plane once the
+        // B update has folded it
+        auto next_a = [&]() {
+            if (more && kA + 2 <= nz) {
+                load_plane(W(iAp), kA + 2);
+                cp_async_commit();
+            }
+        };
+        if (Bok) {
+            if (!Aok) load_b(bb, kB);
+            fused_tile<F, SPLIT>(op, W(iBc), W(iAp), W(iA), bb, q, vout, ps, cs, kB, y0, ny, true,
+                                 next_a);
+        } else {
+            next_a();
+        }
+        __syncthreads();
+        // the B plane above the next A plane into this step's B slot
+        if (more && kA + 3 <= nz) {
+            load_plane(W(iBc), kA + 3);
+            cp_async_commit();
+        }
+        const int oAp = iAp, oBc = iBc;
+        iAp = iA;
+        iA = oAp;
+        iBc = iBn;
+        iBn = oBc;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // the last CTA to finish advances the launch count
+    if (t == 0) {
+        __threadfence();
+        if (atomicAdd(sy.done, 1) == (int)gridDim.x - 1) {
+            atomicExch(sy.done, 0);
+            __threadfence();
+            atomicExch(sy.epoch, want);
+        }
+    }
+}
+
+// co-resident CTAs of the fused kernel per device and row length (64, 128,
+// 192, 256 nodes; set by smoother_init)
+int g_fused_slots[64][kPersMaxNx / 64];
+
+inline int fused_nstrips(const Dims &d) { return (d.ny + kPersTY - 1) / kPersTY; }
+
+// runs along z per strip: as many as fit beside the other strips' runs with
+// all CTAs co-resident, at most one per step
+inline int fused_kz(const Dims &d, int slots) {
+    const int nsteps = d.nz / 2, ns = fused_nstrips(d);
+    int kz = slots / ns;
+    return kz < 1 ? 0 : (kz > nsteps ? nsteps : kz);
+}
+
+template <int F, bool SPLIT>
+cudaError_t launch_fused(const Dims &d, const FineRowsOp &op, const float *b, const float *vin,
+                         float *vout, int kA0, int kz, const SweepSync &sy, cudaStream_t s) {
+    const int nsteps = d.nz / 2, ns = fused_nstrips(d);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ns * kz);
+    cfg.blockDim = dim3(d.nx / 2);
+    cfg.dynamicSmemBytes = fused_floats(d.nx) * sizeof(float);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gs_rows_f<F, SPLIT>, d, op, b, vin, vout, kA0,
+                                             nsteps, ns, kz, sy);
+    count_launch();
+    return e;
+}
+
 // whether the persistent kernel takes this grid; sms set
 bool rows_p_shape(const Dims &d, int &sms) {
     int dev = 0;
@@ -773,18 +1140,67 @@ cudaError_t smoother_init() {
     SET((k_gs_rows_p<FineRowsOp, 0, true, true>), smem_p)
     SET((k_gs_rows_p<CoarseRowsOp, 0, false, false>), smem_p)
     SET((k_gs_rows_p<CoarseRowsOp, 1, false, false>), smem_p)
+    const int smem_f = (int)(fused_floats(kPersMaxNx) * sizeof(float));
+    SET((k_gs_rows_f<0, false>), smem_f)
+    SET((k_gs_rows_f<0, true>), smem_f)
+    SET((k_gs_rows_f<1, false>), smem_f)
+    SET((k_gs_rows_f<1, true>), smem_f)
 #undef SET
+    // co-resident CTAs of the fused kernel for each row length it takes
+    if (dev >= 0 && dev < 64)
+        for (int w = 1; w <= kPersMaxNx / 64; w++) {
+            const int nx = 64 * w;
+            int lo = 1 << 30;
+            const void *kerns[4] = {(const void *)k_gs_rows_f<0, false>,
+                                    (const void *)k_gs_rows_f<0, true>,
+                                    (const void *)k_gs_rows_f<1, false>,
+                                    (const void *)k_gs_rows_f<1, true>};
+            for (const void *kf : kerns) {
+                int nb = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &nb, kf, nx / 2, fused_floats(nx) * sizeof(float));
+                if (e != cudaSuccess) return e;
+                lo = nb < lo ? nb : lo;
+            }
+            g_fused_slots[dev][w - 1] = lo * g_sms[dev];
+        }
     return cudaSuccess;
+}
+
+bool fused_sweep_sizes(const Dims &d, long &naflag, long &npflag, long &nxbuf) {
+    int sms = 0, dev = 0;
+    if (!rows_p_shape(d, sms) || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return false;
+    const int kz = fused_kz(d, g_fused_slots[dev][d.nx / 64 - 1]);
+    if (kz < 1) return false;
+    const long ns = fused_nstrips(d);
+    naflag = ns * (d.nz / 2 + 1);
+    npflag = ns * kz;
+    nxbuf = ns * kz * kPersTY * 3L * d.nx;
+    return true;
 }
 
 // one 8-colour sweep vin -> vout with the row-strip kernels, or
 // cudaErrorNotSupported if the rows are too long for them
 cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
                                const float *vin, float *vout, bool descending, cudaStream_t s,
-                               int split) {
+                               int split, const SweepSync *sync) {
     int sms = 0;
     if (rows_p_ok(d, b, vin, vout, sms)) {
         const FineRowsOp op{f};
+        int dev = 0;
+        const int kz = sync && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64
+                           ? fused_kz(d, g_fused_slots[dev][d.nx / 64 - 1])
+                           : 0;
+        if (kz > 0) {
+            // ascending: A = even planes from 2 (colours 0-3, F = 0);
+            // descending: A = odd planes from 1 (colours 7-4, F = 1)
+            if (!descending)
+                return split ? launch_fused<0, true>(d, op, b, vin, vout, 2, kz, *sync, s)
+                             : launch_fused<0, false>(d, op, b, vin, vout, 2, kz, *sync, s);
+            return split ? launch_fused<1, true>(d, op, b, vin, vout, 1, kz, *sync, s)
+                         : launch_fused<1, false>(d, op, b, vin, vout, 1, kz, *sync, s);
+        }
         return split ? rows_p_sweep<FineRowsOp, true>(d, op, b, vin, vout, descending, s, sms)
                      : rows_p_sweep<FineRowsOp, false>(d, op, b, vin, vout, descending, s, sms);
     }

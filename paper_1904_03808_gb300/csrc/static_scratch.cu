@@ -3,11 +3,10 @@
 //
 // The fine-level residual that the allocating path keeps in a buffer made by
 // mg_setup lives here in one fixed array compiled into the library.  Host
-// code cannot use the array's name as a device address, so the first call
-// on each device looks the address up with cudaGetSymbolAddress (with that
-// device current) and caches it.
-#include <mutex>
-
+// code cannot use the array's name as a device address, so every call looks
+// the address up with cudaGetSymbolAddress on the current device.  The lookup
+// is not cached: after a cudaDeviceReset the module is loaded again, possibly
+// at another address, and a cached pointer would be stale.
 #include "../../include/qsmg.h"
 #include "qsmg_impl.h"
 
@@ -17,13 +16,9 @@ namespace {
 
 // 16 MiB: fine grids with 3 (nz+1) ny nx <= 2097152 corner values
 constexpr long kStaticResidualDoubles = 2097152;
-constexpr int kMaxDevices = 64;
 
 // every GPU that loads the library holds this array until the process exits
 static __device__ __align__(256) double g_static_residual[kStaticResidualDoubles];
-
-std::mutex g_addr_mu;
-double *g_addr[kMaxDevices];  // device address of g_static_residual, per device
 
 }  // namespace
 
@@ -51,27 +46,15 @@ extern "C" mg_status mg_residual_restrict_static(const mg_grid *grid, const mg_m
         set_last_error("mg_residual_restrict_static: need mu > 0 and lambda + mu > 0");
         return MG_ERR_ARG;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        set_last_error("mg_residual_restrict_static: cudaGetDevice: %s", cudaGetErrorString(e));
+    // the device address of the array in the current device's context
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_residual);
+    if (e != cudaSuccess || !p) {
+        set_last_error("mg_residual_restrict_static: cudaGetSymbolAddress: %s",
+                       cudaGetErrorString(e));
         return MG_ERR_CUDA;
     }
-    double *r = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_addr_mu);
-        if (!g_addr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_static_residual);
-            if (e != cudaSuccess || !p) {
-                set_last_error("mg_residual_restrict_static: cudaGetSymbolAddress: %s",
-                               cudaGetErrorString(e));
-                return MG_ERR_CUDA;
-            }
-            g_addr[dev] = (double *)p;
-        }
-        r = g_addr[dev];
-    }
+    double *r = (double *)p;
     // finest-level operator coefficients (scaled Eq. 30, stencils of section 3.4)
     Fine<double> f;
     f.lp = (lam + 2.0 * mu) / mu;

@@ -1,10 +1,13 @@
 """GPU parity: every kernel of the CUDA path, called through the C ABI, against
 the FP64 CPU oracle on the same seeded inputs.
 
-Tolerances: FP64 kernels agree to 1e-12 relative (norm of the difference over
-the norm of the oracle result); FP32 smoothing agrees to the FP32 round-off
-level; the mixed solve reaches the same 1e-10 relative residual and its
-error against the FP64 oracle solution is bounded and reported.
+Tolerances: FP64 kernels agree to 1e-12 relative; FP32 smoothing agrees to
+the FP32 round-off level (2e-6 relative, about 30 units of FP32 rounding:
+each node update sums some 60 products); the mixed solve reaches the same
+1e-10 relative residual and its error against the FP64 oracle solution is
+bounded and reported.  Every comparison is both norm-wise and element-wise:
+``rel`` is the larger of |a - b|_2 / |b|_2 and max|a - b| / max|b|, so a
+localised error (a wall row, a strip seam) cannot hide under a norm.
 """
 import numpy as np
 import pytest
@@ -30,7 +33,11 @@ def c(t):
 
 
 def rel(a, b):
-    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+    """max(|a - b|_2 / |b|_2, max|a - b| / max|b|)."""
+    d = (np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64)).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return max(np.linalg.norm(d) / max(np.linalg.norm(b), 1e-300),
+               np.abs(d).max(initial=0.0) / max(np.abs(b).max(initial=0.0), 1e-300))
 
 
 SHAPES = [(8, 8, 8), (16, 16, 16), (24, 16, 8), (16, 8, 12), (8, 12, 6), (32, 32, 32)]
@@ -143,6 +150,40 @@ def test_smoother_fp32_fine_level(shape):
     assert rel(c(xg), x32) <= 2e-6
 
 
+# the bench's level shapes in miniature: finest rows of 128, 192 and 256
+# nodes (persistent row strips), coarse rows of 128 (row strips with the
+# 27-point operator), 64 x 64 coarse planes (27-point tile kernel), coarse
+# planes of at most 32 x 32 nodes (whole-plane kernel)
+FP32_LEVEL_SHAPES = [(256, 64, 32), (128, 128, 64), (192, 24, 16), (256, 32, 32)]
+
+
+@pytest.mark.parametrize("shape", FP32_LEVEL_SHAPES)
+@pytest.mark.parametrize("descending", [False, True])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_smoother_fp32_every_level_against_oracle(shape, descending, flags):
+    """Every FP32 sweep kernel the mixed solve runs at the bench's shapes
+    (flags 0: the two-phase kernels; flags 1: eight colour launches) against
+    the oracle's colour passes on the same FP32-rounded inputs, two sweeps,
+    both colour orders, non-zero walls on the finest level."""
+    rng = np.random.default_rng(31)
+    ctx = ctx_for(shape, precision=MG_MIXED, flags=flags)
+    mg = O.MG(*shape, LAM, MU)
+    for l in range(mg.levels - 1):
+        d = mg.dims(l)
+        x = rand_corner(rng, d, walls=(l == 0)).astype(np.float32).astype(np.float64)
+        b = rand_corner(rng, d).astype(np.float32).astype(np.float64)
+        xg = g(x, torch.float32)
+        ctx.smooth(l, g(b, torch.float32), xg, 2, descending)
+        S = mg.stencil(l)
+        for _ in range(2):
+            for col in (range(7, -1, -1) if descending else range(8)):
+                O.gs_colour(S, b, x, col)
+        got = c(xg)
+        assert np.array_equal(got[:, [0, d[2]]], x[:, [0, d[2]]])
+        assert rel(got, x) <= 2e-6, (l, rel(got, x))
+    ctx.close()
+
+
 @pytest.mark.parametrize("shape", [(72, 40, 16), (16, 8, 12), (8, 4, 2), (136, 72, 32), (64, 32, 32),
                                    (10, 16, 16), (1024, 64, 64), (256, 32, 32), (128, 40, 32),
                                    (512, 32, 32), (192, 24, 16), (384, 32, 32), (768, 64, 64)])
@@ -175,6 +216,37 @@ def test_tiled_fp32_sweep_equals_colour_passes(shape, sweeps, descending):
         assert rel(outs[0], outs[1]) <= 1e-6, l
     for ctx in ctxs:
         ctx.close()
+
+
+# finest grids whose rows the fused one-launch sweep takes: rows of 64-256
+# nodes, ragged strips (ny = 40: 6 strips of 6 rows and one of 4), several
+# runs along z per strip where the strips leave room
+FUSED_SHAPES = [(256, 32, 32), (128, 40, 32), (64, 32, 32), (192, 24, 16), (256, 64, 32),
+                (128, 128, 64), (64, 64, 64)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES)
+@pytest.mark.parametrize("sweeps,descending", [(1, False), (2, False), (1, True), (3, True)])
+def test_fused_sweep_equals_two_phase(shape, sweeps, descending):
+    """The fused finest-level sweep (both k-parities in one launch, with ready
+    flags between neighbouring strips and a recomputed lead-in plane at the
+    start of each run along z) gives the two-launch sweep's result: every
+    node update sees the same neighbour values, so the results agree to
+    rounding (element-wise), non-zero walls included."""
+    from paper_1904_03808_gb300.binding import MG_FLAG_TWO_PHASE
+    rng = np.random.default_rng(13)
+    nx, ny, nz = shape
+    x = rng.uniform(-1, 1, (3, nz + 1, ny, nx)).astype(np.float32)
+    b = rng.uniform(-1, 1, (3, nz + 1, ny, nx)).astype(np.float32)
+    outs = []
+    for flags in (0, MG_FLAG_TWO_PHASE):
+        ctx = ctx_for(shape, precision=MG_MIXED, flags=flags)
+        xg = g(x, torch.float32)
+        ctx.smooth(0, g(b, torch.float32), xg, sweeps, descending)
+        outs.append(c(xg))
+        ctx.close()
+    assert np.array_equal(outs[0][:, [0, nz]], x[:, [0, nz]])
+    assert rel(outs[0], outs[1]) <= 1e-6
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -275,13 +347,14 @@ def test_mixed_solve_reaches_tolerance(shape, inner):
 
 
 @pytest.mark.parametrize("inner", [0, 4])
-def test_mixed_graph_replay_equals_direct_launches(inner):
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 32)])
+def test_mixed_graph_replay_equals_direct_launches(inner, shape):
     """The FP32 inner cycles replayed from CUDA graphs give bitwise the same
-    iterate as the same kernels launched one by one."""
-    shape = (32, 32, 32)
+    iterate as the same kernels launched one by one (at 64 x 64 x 32 the
+    finest sweeps are the fused cooperative launches)."""
     b = I.rhs_field(4, *shape)
     v = np.zeros_like(b)
-    v[0, 0], v[0, 32] = -1.0, 1.0
+    v[0, 0], v[0, shape[2]] = -1.0, 1.0
     outs = []
     for flags in (0, 2):
         ctx = ctx_for(shape, precision=MG_MIXED, max_cycles=30, inner_cycles=inner, flags=flags)
@@ -487,7 +560,17 @@ def test_fullsize_bench_step_256():
     S = O.fine_stencil(LAM, MU)
     v0 = vn.copy()
     v0[:, 1:w.nz] = 0.0
-    rel_resid = np.sqrt(O.norm2(O.residual(S, b, vn)) / O.norm2(O.residual(S, b, v0)))
-    assert rel_resid <= 2.0 * bench.TOL, rel_resid
+    bl2 = O.norm2(O.residual(S, b, v0))
+    rel_resid = np.sqrt(O.norm2(O.residual(S, b, vn)) / bl2)
+    # the library and the oracle sum the residual's 57 terms a node in
+    # different orders: their values differ by at most a few ulps of
+    # |A||v| + |b| a node, which bounds the difference of the two relative
+    # residuals (the walls make |v| large against the lifted right-hand side)
+    absS = np.abs(S)
+    mag = O.apply(absS, np.abs(vn)) + np.abs(b)
+    mag[:, [0, w.nz]] = 0.0
+    floor = 64 * np.finfo(np.float64).eps * np.sqrt(O.norm2(mag) / bl2)
+    assert abs(rel_resid - s.rel_resid) <= floor, (rel_resid, s.rel_resid, floor)
+    assert rel_resid <= bench.TOL + floor, (rel_resid, floor)
     assert rel(c(sg), O.stress_final(vn, ss, w.h, w.dt, LAM, MU)) <= 1e-11
     assert rel(c(cg), O.chi_update(sig, chi, D, sb, w.h, w.dt, p)) <= 1e-12

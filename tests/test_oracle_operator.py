@@ -295,3 +295,44 @@ def test_same_colour_nodes_do_not_couple():
                             f -= lvl_S[d] @ xb[:, k + dz, (j + dy) % ny, (i + dx) % nx]
                 xb[:, k, j, i] = np.linalg.solve(lvl_S[13], f)
         assert np.allclose(xo, xb, rtol=1e-13, atol=1e-13)
+
+
+def test_galerkin_stencils_keep_the_reflection_symmetry():
+    """Reflecting one axis maps the elastic problem of Eq. (30) onto itself
+    with that velocity component negated, and trilinear T commutes with the
+    reflection, so every Galerkin level (Eq. 36) keeps the fine stencil's
+    parity structure: with A(d) the 3x3 block of offset d = (dx, dy, dz),
+      - A(d)_aa is even in each of dx, dy, dz;
+      - A(d)_ab (a != b) is odd in d_a and in d_b and even in the third
+        offset, hence zero unless d_a and d_b are both non-zero (153 of the
+        243 entries can be non-zero);
+      - A(-d) = A(d)^T.
+    Checked on the fine stencil and six Galerkin levels (the coarse kernels
+    store one coefficient per parity class: 21 diagonal and 6 coupling)."""
+    S = O.fine_stencil(LAM, MU)
+    for level in range(7):
+        T = S.reshape(3, 3, 3, 3, 3)  # [dz+1, dy+1, dx+1, a, b]
+        scale = np.abs(S).max()
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    d = (dx, dy, dz)
+                    A = T[dz + 1, dy + 1, dx + 1]
+                    assert np.allclose(A, T[1 - dz, 1 - dy, 1 - dx].T, rtol=0, atol=1e-14 * scale)
+                    for a in range(3):
+                        for b in range(3):
+                            # flip each axis in turn
+                            for ax in range(3):
+                                e = list(d)
+                                e[ax] = -e[ax]
+                                Ae = T[e[2] + 1, e[1] + 1, e[0] + 1]
+                                sign = (-1 if ax == a else 1) * (-1 if ax == b else 1)
+                                assert abs(Ae[a, b] - sign * A[a, b]) <= 1e-14 * scale, \
+                                    (level, d, a, b, ax)
+                            if a != b and (d[a] == 0 or d[b] == 0):
+                                assert abs(A[a, b]) <= 1e-14 * scale, (level, d, a, b)
+        nz = sum(1 for v in S.ravel() if abs(v) > 1e-14 * np.abs(S).max())
+        assert nz <= 153
+        if level >= 1:
+            assert nz == 153  # every admissible coupling appears on coarse levels
+        S = O.galerkin(S)
