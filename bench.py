@@ -60,8 +60,8 @@ def parse():
     ap.add_argument("--inner", type=int, default=INNER)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-only", action="store_true")
-    ap.add_argument("--two-phase", action="store_true",
-                    help="--sweep-only: the two-launch finest sweep instead of the fused one")
+    ap.add_argument("--fused", action="store_true",
+                    help="--sweep-only: the fused one-launch finest sweep (MG_FLAG_FUSED_SWEEP)")
     ap.add_argument("--disc", action="store_true")
     ap.add_argument("--dt-ts", type=float, default=2.0e4)
     ap.add_argument("--kind", type=int, default=1, choices=[1, 2, 3],
@@ -170,9 +170,9 @@ def run_sweeps(args):
     nz = args.nz or n
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
-    from paper_1904_03808_gb300.binding import MG_FLAG_TWO_PHASE
+    from paper_1904_03808_gb300.binding import MG_FLAG_FUSED_SWEEP
     ctx = Context(n, n, nz, 2.0e-2 / n, I.TABLE1["K"], I.TABLE1["mu"], precision=MG_MIXED,
-                  stream=stream, flags=MG_FLAG_TWO_PHASE if args.two_phase else 0)
+                  stream=stream, flags=MG_FLAG_FUSED_SWEEP if args.fused else 0)
     g = torch.Generator(device=dev).manual_seed(5)
     x = torch.rand((3, nz + 1, n, n), device=dev, dtype=torch.float32, generator=g) - 0.5
     b = torch.rand((3, nz + 1, n, n), device=dev, dtype=torch.float32, generator=g) - 0.5
@@ -190,7 +190,7 @@ def run_sweeps(args):
     ctx.close()
     t = sm_ms / max(sweeps, 1)
     nodes = n * n * (nz - 1)
-    return {"mode": "sweep-only", "kernel": "two-phase" if args.two_phase else "default",
+    return {"mode": "sweep-only", "kernel": "fused" if args.fused else "two-phase",
             "grid": [n, n, nz], "sweeps": sweeps, "sweep_ms": t,
             "achieved_gbs": SMOOTH_BYTES * nodes / (t / 1e3) / 1e9,
             "launches_per_sweep": launches / max(sweeps, 1), "clocks": clk}

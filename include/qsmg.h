@@ -57,7 +57,7 @@ enum { MG_FP64 = 0, MG_MIXED = 1 };
 enum {
     MG_FLAG_COLOUR_PASSES = 1, /* FP32 sweeps: one launch per colour */
     MG_FLAG_NO_GRAPH = 2,      /* FP32 inner cycles: plain launches, no CUDA graph */
-    MG_FLAG_TWO_PHASE = 4      /* finest FP32 sweeps: one launch per k-parity */
+    MG_FLAG_FUSED_SWEEP = 4    /* finest FP32 sweeps: both k-parities in one launch */
 };
 enum { MG_HIST = 128 };
 
@@ -104,10 +104,12 @@ typedef struct {
  *                 eight colour launches instead of the two-phase kernels
  *                 (row strips, whole planes, tiles); MG_FLAG_NO_GRAPH issues the FP32 inner cycles as
  *                 plain launches instead of replaying a CUDA graph captured
- *                 at their first use; MG_FLAG_TWO_PHASE runs the finest-level
- *                 FP32 sweep as two launches (the planes of one k-parity,
- *                 then the other) where the fused one-launch sweep would
- *                 apply (same arithmetic; kept for comparison).
+ *                 at their first use; MG_FLAG_FUSED_SWEEP runs each
+ *                 finest-level FP32 sweep as one cooperative launch (both
+ *                 k-parities, with ready flags between neighbouring row
+ *                 strips) instead of two, where the grid suits it: a third
+ *                 less DRAM traffic, but slower on GB300 (same arithmetic;
+ *                 kept for comparison).
  */
 typedef struct {
     int precision;

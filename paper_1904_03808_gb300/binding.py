@@ -21,7 +21,7 @@ MG_OK, MG_ERR_ARG, MG_ERR_SHAPE, MG_ERR_CUDA, MG_ERR_OOM, MG_ERR_NOCONV, MG_ERR_
 MG_FP64, MG_MIXED = 0, 1
 MG_FLAG_COLOUR_PASSES = 1
 MG_FLAG_NO_GRAPH = 2
-MG_FLAG_TWO_PHASE = 4
+MG_FLAG_FUSED_SWEEP = 4
 MG_HIST = 128
 
 

@@ -958,12 +958,11 @@ mg_status mg_setup(const mg_grid *grid, const mg_moduli *moduli, const mg_bc *bc
         ALLOC(ctx->rhs, corner_count(ctx->L[0]));
     }
     {
-        long na = 0, np_ = 0, nb = 0;
-        if (!(opts->flags & (MG_FLAG_COLOUR_PASSES | MG_FLAG_TWO_PHASE)) && ctx->nlev > 1 &&
-            fused_sweep_sizes(ctx->L[0], na, np_, nb)) {
+        long na = 0;
+        if ((opts->flags & MG_FLAG_FUSED_SWEEP) && !(opts->flags & MG_FLAG_COLOUR_PASSES) &&
+            ctx->nlev > 1 &&
+            fused_sweep_sizes(ctx->L[0], na)) {
             ALLOC(ctx->sync.aflag, (size_t)na);
-            ALLOC(ctx->sync.pflag, (size_t)np_);
-            ALLOC(ctx->sync.xbuf, (size_t)nb);
             ALLOC(ctx->sync.epoch, (size_t)1);
             ALLOC(ctx->sync.done, (size_t)1);
             ALLOC(ctx->sync.err, (size_t)1);

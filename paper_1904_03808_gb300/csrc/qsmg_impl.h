@@ -142,18 +142,14 @@ cudaError_t gs_sweep_coarse_rows(const Dims &d, const Coarse<float> &c, const fl
                                  const float *vin, float *vout, bool descending, cudaStream_t s);
 // Cross-CTA state of the fused finest-level sweep (device memory, zeroed at
 // allocation, owned by the context): per-tile ready flags that hold the
-// launch count + 1 once the tile is done, the exchange rows of each chunk's
-// lead-in tile, the launch count, and an error word set when a bounded wait
-// gives up.  Sized by fused_sweep_sizes.
+// launch count + 1 once the tile is stored, the launch count, the CTAs done
+// in the current launch, and an error word set when a bounded wait gives up.
 struct SweepSync {
-    int *aflag;   // [nstrips][nsteps + 1]
-    int *pflag;   // [nchunks]
-    float *xbuf;  // [nchunks][6 strip rows][3][nx]
+    int *aflag;  // [row strips][nz / 2 + 1]
     int *epoch, *done, *err;
 };
-// whether the fused sweep takes this grid, and the sizes of its SweepSync
-// arrays (in elements); false if it does not apply
-bool fused_sweep_sizes(const Dims &d, long &naflag, long &npflag, long &nxbuf);
+// whether the fused sweep takes this grid, and the length of its flag array
+bool fused_sweep_sizes(const Dims &d, long &naflag);
 // FP32 finest-level sweep vin -> vout with the row-strip kernels: the fused
 // one-launch sweep when sync is given and the grid suits it, else the two
 // phase launches; cudaErrorNotSupported when the rows are too long for them

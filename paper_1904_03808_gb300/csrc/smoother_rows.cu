@@ -731,37 +731,59 @@ cudaError_t rows_p_sweep(const Dims &d, const OP &op, const float *b, const floa
 }
 
 // ------------------------------------------------------------------------
-// Fused sweep: both phases of an 8-colour sweep in one launch, so that v is
-// read from DRAM once per sweep instead of once per phase.  The planes of the
-// first phase ("A": the even planes, colours 0-3, in an ascending sweep; the
-// odd ones, colours 7-4, in a descending sweep) depend only on the sweep's
-// input; a plane of the second phase ("B") needs the new values of the A
-// planes just below and above it.  Each CTA owns one row strip of TY rows
-// and a contiguous run of "steps" along z; step m updates A plane
-// kA(m) = kA0 + 2 (m - 1) and then B plane kA(m) - 1, whose z-neighbours
-// are the A planes of steps m - 1 and m, both still in shared memory.  The
-// window rows of a new A plane outside the strip come from the neighbouring
-// strips' CTAs: each publishes a ready flag per (strip, step) after storing
-// its tile, and a CTA waits for the flags of the rows it needs before it
-// copies them (from L2: they were just written).  A run that does not start
-// at step 1 first recomputes the A plane of the step before it (exactly as
-// the run below computes it) and exchanges that tile's boundary rows with
-// its neighbours through a small buffer, so runs along z never wait on each
-// other.  All CTAs are co-resident (cooperative launch); every wait is
-// bounded and sets the error word when it gives up (the sweep then carries
-// on with whatever it read, and the host reports the error).
+// Fused sweep: both phases of an 8-colour sweep in one launch, so that each
+// value of v comes from DRAM once per sweep instead of once per phase.  The
+// planes of the first phase ("A": the even planes, colours 0-3, in an
+// ascending sweep; the odd ones, colours 7-4, in a descending sweep) depend
+// only on the sweep's input; a plane of the second phase ("B") needs the new
+// values of the A planes just below and above it.  Number the A planes by
+// step m = 1, 2, ...: kA(m) = kA0 + 2 (m - 1), and let B plane kB(m) =
+// kA(m) - 1 go with it; B(m) needs A(m - 1) and A(m).
 //
-// Shared memory: four windows of R rows x 3 components x nx (110.6 KB at
-// nx = 256, two CTAs per SM): the A plane being updated, the new A plane of
-// the previous step, the old B plane of this step (updated in place by the
-// second phase) and the old B plane above the A plane.  Right-hand-side rows
-// are loaded from global memory into registers.
+// Each CTA owns one row strip and runs over short chunks of steps along z:
+// in chunk [m0, m1) it updates the strip's tiles of A planes m0 .. m1-1,
+// then those of B planes m0 .. m1-1.  A B tile reads its own old plane
+// (which the A tiles of the chunk just read as a z-neighbour) and the new A
+// planes around it (which the chunk, its neighbouring strips' chunks and the
+// chunk below just wrote), so both mostly come from L2; only b and the old A
+// planes come from DRAM.  The tile loop is the persistent kernel's: each
+// tile's operands are copied into shared memory while the previous tile is
+// computed, with the z-plane slots reused between consecutive tiles.  Before
+// copying a new A plane's window rows, a CTA waits for the ready flags of the
+// strips that own them (published after each A tile's store by a barrier
+// and a release store; read with a relaxed load a tile ahead, then again
+// with an acquire
+// load once seen set).  The steps are cut into fused_rounds bands of K
+// chunks each; in round r the K CTAs of a strip take the K chunks of band r,
+// the l-th CTA chunk (l + r) mod K (rotated so that the CTAs' loads match),
+// so a B tile waits only on A tiles of the same or an earlier round,
+// whose CTAs are running or done: the cooperative launch keeps every CTA
+// resident, and no A tile waits on anything.  Every wait is bounded
+// and sets the error word when it gives up (the sweep then carries on with
+// what it read, and the host reports the error).
+//
+// Measured on GB300 against the two-launch sweep (k_gs_rows_p): 33 against
+// 49 B of DRAM traffic a node and an L2 hit rate of 63 against 12%, but
+// 0.199 against 0.178 ms a 256^3 sweep (0.108 against 0.101 at
+// 256 x 256 x 128).  Both kernels are latency-bound at 8 warps an SM (no
+// unit above 53% of its peak), so the DRAM they save buys no time, and the
+// flag reads, the extra barrier of a B tile and the shorter runs of z-plane
+// reuse cost about 10%.  Selected by MG_FLAG_FUSED_SWEEP; the two-launch
+// sweep stays the default.
 
 constexpr long kSpinMax = 1L << 22;  // flag polls before a wait gives up (about 2 s)
+// chunks per CTA: enough that the A planes a chunk writes are still in L2
+// when its B tiles read them (about 2-3 steps a chunk)
+__host__ __device__ constexpr int fused_rounds(int nsteps) { return nsteps >= 128 ? 8 : 4; }
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void st_release(int *p, int v) {
@@ -778,94 +800,17 @@ __device__ __forceinline__ void wait_flag(const int *f, int want, int *err) {
     atomicOr(err, 1);
 }
 
-constexpr int kFusedWindows = 4;
-__host__ __device__ constexpr long fused_floats(int nx) {
-    return (long)kFusedWindows * 3 * kPersR * nx;
-}
-
-// one tile update of plane k (window Wk, in place) with z-neighbour windows
-// WL, WH and right-hand side bb; after_fold runs once every thread has
-// folded (WL and WH are then free); the final tile values are left in Wk
-// (every pass writes its nodes there) and, if store, in plane k of vout
-template <int F, bool SPLIT, class AF>
-__device__ __forceinline__ void fused_tile(const FineRowsOp &op, float *Wk, const float *WL,
-                                           const float *WH, const float (&bb)[3][2][kPersR],
-                                           const RowCols &q, float *vout, long ps, long cs,
-                                           int k, int y0, int ny, bool store, const AF &after_fold) {
-    constexpr int TY = kPersTY, R = kPersR;
-    float r[3][2][R];
-    auto bv = [&](int jj, int c, int e) { return bb[c][e][jj]; };
-    op.template fold_with<R>(r, WL, WH, bv, q);
-    float P[3][2][R];
-#pragma unroll
-    for (int c = 0; c < 3; c++)
-#pragma unroll
-        for (int jj = 0; jj < R; jj++) {
-            P[c][0][jj] = Wk[q.at(jj, c, q.xe)];
-            P[c][1][jj] = Wk[q.at(jj, c, q.xo)];
-        }
-    __syncthreads();
-    after_fold();
-    constexpr int EF = F, EG = 1 - F;
-    const int xF = EF == 0 ? q.xe : q.xo, xG = EG == 0 ? q.xe : q.xo;
-    // pass 1: x-parity F on the odd rows
-#pragma unroll
-    for (int jj = 1; jj < R - 1; jj += 2) {
-        pers_update<EF, R>(op, P, r, Wk, q, jj);
-#pragma unroll
-        for (int c = 0; c < 3; c++) Wk[q.at(jj, c, xF)] = P[c][EF][jj];
-    }
-    __syncthreads();
-    // pass 2: x-parity 1-F on the odd rows
-#pragma unroll
-    for (int jj = 1; jj < R - 1; jj += 2) {
-        pers_update<EG, R>(op, P, r, Wk, q, jj);
-#pragma unroll
-        for (int c = 0; c < 3; c++) Wk[q.at(jj, c, xG)] = P[c][EG][jj];
-    }
-    __syncthreads();
-    // pass 3: x-parity F on the even rows
-#pragma unroll
-    for (int jj = 2; jj < R - 2; jj += 2) {
-        pers_update<EF, R>(op, P, r, Wk, q, jj);
-#pragma unroll
-        for (int c = 0; c < 3; c++) Wk[q.at(jj, c, xF)] = P[c][EF][jj];
-    }
-    __syncthreads();
-    // pass 4: x-parity 1-F on the even rows (its readers read only the
-    // other parity's columns, so the results can go to Wk at once)
-#pragma unroll
-    for (int jj = 2; jj < R - 2; jj += 2) {
-        pers_update<EG, R>(op, P, r, Wk, q, jj);
-#pragma unroll
-        for (int c = 0; c < 3; c++) Wk[q.at(jj, c, xG)] = P[c][EG][jj];
-    }
-    if (store) {
-        float *Ok = vout + (long)k * ps;
-#pragma unroll
-        for (int jj = 1 + F; jj < TY + 1 + F; jj++) {
-            const int y = y0 - 1 - F + jj;
-            if (y < ny) {
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    Ok[c * cs + (long)y * q.nx + q.xe] = P[c][0][jj];
-                    Ok[c * cs + (long)y * q.nx + q.xo] = P[c][1][jj];
-                }
-            }
-        }
-    }
-}
-
 template <int F, bool SPLIT>
 __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
     k_gs_rows_f(Dims d, FineRowsOp op, const float *__restrict__ b, const float *__restrict__ vin,
-                float *__restrict__ vout, int kA0, int nsteps, int nstrips, int kz, SweepSync sy) {
+                float *__restrict__ vout, int kA0, int nsteps, int nstrips, int K, SweepSync sy) {
     constexpr int TY = kPersTY, R = kPersR;
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_epoch;
     const int nx = d.nx, ny = d.ny, nz = d.nz, hn = nx >> 1, cpr = nx >> 2;
     const long ps = (long)nx * ny, cs = d.cs;
-    const int win = 3 * R * nx;
+    const int plane_f = 3 * R * nx, bst_f = 3 * (R - 2) * nx;
+    float *const Ps = sm, *const Bs = sm + plane_f, *const Zs0 = Bs + bst_f;
     const int t = threadIdx.x;
     const int q4 = 4 * (t % cpr), g = t / cpr;
     const int tm = t == 0 ? hn - 1 : t - 1, tp = t + 1 == hn ? 0 : t + 1;
@@ -875,182 +820,216 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
     q.xo = SPLIT ? hn + t : 2 * t + 1;
     q.xom = SPLIT ? hn + tm : 2 * tm + 1;
     q.xep = SPLIT ? tp : 2 * tp;
-    const int chunk = blockIdx.x, s = chunk % nstrips, zc = chunk / nstrips;
-    const int m0 = 1 + (int)((long)zc * nsteps / kz), m1 = 1 + (int)((long)(zc + 1) * nsteps / kz);
-    const int y0 = s * TY, slen = ny - y0 < TY ? ny - y0 : TY;
+    const int s = blockIdx.x % nstrips, lane = blockIdx.x / nstrips;
+    const int y0 = s * TY;
+    const int NR = fused_rounds(nsteps);
     if (t == 0) s_epoch = *(volatile int *)sy.epoch;
     __syncthreads();
     const int want = s_epoch + 1;
-    // window slot i (its role changes from step to step)
-    auto W = [&](int i) { return sm + i * win; };
-    int iAp = 0, iA = 1, iBc = 2, iBn = 3;
 
-    // grid row of window row jj (wrapped) and whether it lies outside the strip
+    // the CTA's tiles in order: round r (chunk lane + K r), phase ph (0: A,
+    // 1: B), i-th tile of the run; step m, plane k.  An A run starts with the
+    // chunk's last step, which the chunk above needs first, then goes up from
+    // m0; a B run goes up from m0.  Valid A tiles have kA <= nz - 1, valid B
+    // tiles kB >= 1
+    struct Tile {
+        int r, ph, i, m, m0, m1, k;
+    };
+    // round r covers band r of the steps, split into K chunks; the CTA of
+    // lane l takes chunk (l + r) mod K, so that every CTA's chunks add up to
+    // the same length within a step, and the chunk below a chunk (the
+    // previous one of the band, or the last one of the band below) is taken
+    // in the same round or the round before
+    auto chunk_of = [&](Tile &U) {
+        const int b0 = 1 + (int)((long)U.r * nsteps / NR);
+        const int bl = 1 + (int)((long)(U.r + 1) * nsteps / NR) - b0;
+        const int j = (lane + U.r) % K;
+        U.m0 = b0 + j * bl / K;
+        U.m1 = b0 + (j + 1) * bl / K;
+    };
+    auto step_of = [&](const Tile &U) {
+        return U.ph == 1 ? U.m0 + U.i : (U.i == 0 ? U.m1 - 1 : U.m0 + U.i - 1);
+    };
+    auto plane_of = [&](const Tile &U) { return kA0 + 2 * (U.m - 1) - U.ph; };
+    // the next valid tile after U (U.r == NR: none)
+    auto advance = [&](Tile &U) {
+        for (;;) {
+            if (++U.i >= U.m1 - U.m0) {
+                if (U.ph == 0) {
+                    U.ph = 1;
+                } else {
+                    U.ph = 0;
+                    if (++U.r >= NR) return;
+                    chunk_of(U);
+                }
+                U.i = 0;
+            }
+            U.m = step_of(U);
+            U.k = plane_of(U);
+            if (U.k >= 1 && U.k <= nz - 1) return;
+        }
+    };
     auto wrow = [&](int jj) {
         const int y = y0 - 1 - F + jj;
         return y < 0 ? y + ny : (y >= ny ? y - ny : y);
     };
-    auto halo = [&](int jj) {
-        const int y = y0 - 1 - F + jj;
-        return y < y0 || y >= y0 + slen;
-    };
-    // window rows [jlo, jhi) of plane k of src into window dst
-    auto copy_rows = [&](float *dst, const float *src, int k, int jlo, int jhi) {
-        const float *base = src + (long)k * ps + q4;
+    // window rows [jlo, jhi) of plane qq of src into dst (rows from jlo)
+    auto copy_rows = [&](float *dst, const float *src, int qq, int jlo, int jhi) {
+        const float *base = src + (long)qq * ps + q4;
         for (int jj = jlo + g; jj < jhi; jj += 2) {
             const float *srow = base + (long)wrow(jj) * nx;
-            float *drow = dst + jj * 3 * nx + q4;
+            float *drow = dst + (jj - jlo) * 3 * nx + q4;
             cp_async16(drow, srow);
             cp_async16(drow + nx, srow + cs);
             cp_async16(drow + 2 * nx, srow + 2 * cs);
         }
     };
-    auto load_plane = [&](float *dst, int k) { copy_rows(dst, vin, k, 0, R); };
-    // right-hand side of window rows 1 .. R-2 of plane k into registers
-    auto load_b = [&](float (&bb)[3][2][R], int k) {
-        const float *Bk = b + (long)k * ps;
-#pragma unroll
-        for (int jj = 1; jj < R - 1; jj++) {
-            const long o = (long)wrow(jj) * nx;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                bb[c][0][jj] = __ldg(Bk + c * cs + o + q.xe);
-                bb[c][1][jj] = __ldg(Bk + c * cs + o + q.xo);
-            }
-        }
-    };
-    auto publish = [&](int *flag) {
-        __syncthreads();
-        if (t == 0) {
-            __threadfence();
-            st_release(flag, want);
-        }
-    };
-    // thread 0 waits for the flags of the owners of the window's halo rows
-    auto wait_owners = [&](const int *flags, long stride, long offset) {
-        if (t == 0) {
-            int last = -1;
-            for (int jj = 0; jj < R; jj++) {
-                if (!halo(jj)) continue;
-                const int o = wrow(jj) / TY;
-                if (o == last) continue;
-                last = o;
-                wait_flag(flags + o * stride + offset, want, sy.err);
-            }
-        }
-        __syncthreads();
-    };
-    const int nop = 0;
-    auto none = [&]() { (void)nop; };
-    float bb[3][2][R];  // right-hand side of the tile being updated
-
-    // ---- lead-in
-    const int kA1 = kA0 + 2 * (m0 - 1);  // A plane of the first step
-    if (m0 > 1) {
-        // recompute the A plane of step m0 - 1 (the run below computes and
-        // stores it); the window slot of this run's first A plane holds its
-        // lower neighbour meanwhile
-        const int kP = kA1 - 2;
-        load_plane(W(iAp), kP);
-        load_plane(W(iA), kP - 1);
-        load_plane(W(iBc), kP + 1);
-        cp_async_commit();
-        load_b(bb, kP);
-        cp_async_wait_all();
-        __syncthreads();
-        fused_tile<F, SPLIT>(op, W(iAp), W(iA), W(iBc), bb, q, vout, ps, cs, kP, y0, ny, false,
-                             none);
-        // its strip rows into the exchange buffer
-        float *xb = sy.xbuf + (long)chunk * TY * 3 * nx;
-        for (int rr = 0; rr < slen; rr++) {
-            const int jj = 1 + F + rr;
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                xb[(rr * 3 + c) * nx + q.xe] = W(iAp)[q.at(jj, c, q.xe)];
-                xb[(rr * 3 + c) * nx + q.xo] = W(iAp)[q.at(jj, c, q.xo)];
-            }
-        }
-        publish(sy.pflag + chunk);
-        // this run's first A plane and the B plane above it
-        load_plane(W(iA), kA1);
-        if (kA1 + 1 <= nz) load_plane(W(iBn), kA1 + 1);
-        cp_async_commit();
-        // the lead-in plane's halo rows from the neighbours' exchange rows
-        wait_owners(sy.pflag, 1, (long)zc * nstrips);
-        for (int jj = 0; jj < R; jj++) {
-            if (!halo(jj)) continue;
-            const int y = wrow(jj), o = y / TY, rr = y - o * TY;
-            const float *src = sy.xbuf + ((long)(zc * nstrips + o) * TY + rr) * 3 * nx;
-            if (g == (jj & 1)) {
-#pragma unroll
-                for (int c = 0; c < 3; c++) cp_async16(W(iAp) + (jj * 3 + c) * nx + q4, src + c * nx + q4);
-            }
-        }
-        cp_async_commit();
-    } else {
-        if (kA1 - 2 >= 0) load_plane(W(iAp), kA1 - 2);  // the wall below (ascending)
-        load_plane(W(iBc), kA1 - 1);
-        load_plane(W(iA), kA1);
-        if (kA1 + 1 <= nz) load_plane(W(iBn), kA1 + 1);
-        cp_async_commit();
+    // z-plane slots 0, 1 (tag: plane; within one sweep a plane number is
+    // always read from the same array: A tiles read old B planes from vin,
+    // B tiles new A planes (or the walls) from vout)
+    int tag0 = -1, tag1 = -1;
+    // the strips owning the window rows (at most 3; fixed for the CTA)
+    int own[3] = {-1, -1, -1}, nown = 0;
+    for (int jj = 0; jj < R; jj++) {
+        const int o = wrow(jj) / TY;
+        if (nown < 3 && (nown == 0 || (own[nown - 1] != o && own[0] != o))) own[nown++] = o;
     }
-
-    // ---- the run's steps
-    for (int m = m0; m < m1; m++) {
-        const int kA = kA0 + 2 * (m - 1), kB = kA - 1;
-        const bool Aok = kA <= nz - 1, Bok = kB >= 1;
-        if (Aok) load_b(bb, kA);
-        cp_async_wait_all();
-        __syncthreads();
-        if (Aok) {
-            fused_tile<F, SPLIT>(op, W(iA), W(iBc), W(iBn), bb, q, vout, ps, cs, kA, y0, ny, true,
-                                 none);
-            // the B tile's right-hand side, in flight during the wait below
-            if (Bok) load_b(bb, kB);
-            publish(sy.aflag + (long)s * (nsteps + 1) + m);
-            // the new plane's window rows outside the strip, from the
-            // neighbours' stores
-            wait_owners(sy.aflag, nsteps + 1, m);
-            const float *Ok = vout + (long)kA * ps + q4;
-            for (int jj = g; jj < R; jj += 2) {
-                if (!halo(jj)) continue;
-                const float *srow = Ok + (long)wrow(jj) * nx;
-                float *drow = W(iA) + jj * 3 * nx + q4;
-                cp_async16(drow, srow);
-                cp_async16(drow + nx, srow + cs);
-                cp_async16(drow + 2 * nx, srow + 2 * cs);
+    // the ready flag for thread idx before a tile's new z-neighbour planes
+    // are copied: for a B tile, those (strip o, step mm) of the owners of
+    // each A plane p = kA(mm) that is not already in a slot (walls need
+    // none); at most 2 planes x 3 owners, one per thread idx < count
+    auto flag_of = [&](const Tile &U, int idx) -> const int * {
+        if (U.r >= NR || U.ph != 1 || idx >= 2 * nown) return nullptr;
+        const int side = idx / nown, o = own[idx - side * nown];
+        const int p = side ? U.k + 1 : U.k - 1, mm = side ? U.m : U.m - 1;
+        if (p <= 0 || p >= nz || tag0 == p || tag1 == p) return nullptr;
+        return sy.aflag + (long)o * (nsteps + 1) + mm;
+    };
+    // whether a B tile needs any flag (the same answer in every thread)
+    auto needs_flags = [&](const Tile &U) {
+        if (U.ph != 1) return false;
+        const int pl = U.k - 1, ph_ = U.k + 1;
+        return (pl > 0 && tag0 != pl && tag1 != pl) || (ph_ < nz && tag0 != ph_ && tag1 != ph_);
+    };
+    // copies of tile U's operands; fp / fv: this thread's flag for U and the
+    // value it read from it earlier (checked, and waited for if not yet set,
+    // before the z-plane copies that depend on it)
+    auto issue_bz = [&](const Tile &U, int &sL, int &sH, const int *fp, int fv) {
+        const int k = U.k;
+        const float *zsrc = U.ph == 0 ? vin : vout;
+        copy_rows(Bs, b, k, 1, R - 1);
+        copy_rows(Ps, vin, k, 0, R);
+        if (needs_flags(U)) {
+            // fv was read a tile ahead without ordering (wait only if it was
+            // not yet set); the acquire load orders this thread's (and,
+            // through the barrier, the CTA's) later reads after the
+            // producer's stores without waiting for this thread's own
+            // copies in flight
+            if (fp) {
+                if (fv < want) wait_flag(fp, want, sy.err);
+                (void)ld_acquire(fp);
             }
-            cp_async_commit();
-            cp_async_wait_all();
             __syncthreads();
         }
-        const bool more = m + 1 < m1;
-        // next step's A plane into the slot of the previous A plane once the
-        // B update has folded it
-        auto next_a = [&]() {
-            if (more && kA + 2 <= nz) {
-                load_plane(W(iAp), kA + 2);
-                cp_async_commit();
+        sL = tag0 == k - 1 ? 0 : (tag1 == k - 1 ? 1 : -1);
+        sH = tag0 == k + 1 ? 0 : (tag1 == k + 1 ? 1 : -1);
+        if (sL < 0) {
+            sL = sH == 0 ? 1 : 0;
+            if (sL == 0)
+                tag0 = k - 1;
+            else
+                tag1 = k - 1;
+            copy_rows(Zs0 + sL * plane_f, zsrc, k - 1, 0, R);
+        }
+        if (sH < 0) {
+            sH = 1 - sL;
+            if (sH == 0)
+                tag0 = k + 1;
+            else
+                tag1 = k + 1;
+            copy_rows(Zs0 + sH * plane_f, zsrc, k + 1, 0, R);
+        }
+        cp_async_commit();
+    };
+
+    Tile T;
+    T.r = 0;
+    T.ph = 0;
+    T.i = -1;
+    chunk_of(T);
+    advance(T);
+    int sL = 0, sH = 1;
+    if (T.r < NR) {
+        const int *fp = flag_of(T, t);
+        issue_bz(T, sL, sH, fp, fp ? ld_relaxed(fp) : want);
+    }
+    while (T.r < NR) {
+        cp_async_wait_all();
+        __syncthreads();
+        // the next tile, and a first read of its flags (one per thread), in
+        // flight while this tile is computed
+        Tile Tn = T;
+        advance(Tn);
+        const int *fp = flag_of(Tn, t);
+        const int fv = fp ? ld_relaxed(fp) : want;
+        float r[3][2][R];
+        op.template fold<R>(r, Zs0 + sL * plane_f, Zs0 + sH * plane_f, Bs, q);
+        float P[3][2][R];
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int jj = 0; jj < R; jj++) {
+                if (SPLIT) {
+                    P[c][0][jj] = Ps[q.at(jj, c, q.xe)];
+                    P[c][1][jj] = Ps[q.at(jj, c, q.xo)];
+                } else {
+                    const float2 v = *reinterpret_cast<const float2 *>(&Ps[q.at(jj, c, q.xe)]);
+                    P[c][0][jj] = v.x;
+                    P[c][1][jj] = v.y;
+                }
             }
-        };
-        if (Bok) {
-            if (!Aok) load_b(bb, kB);
-            fused_tile<F, SPLIT>(op, W(iBc), W(iAp), W(iA), bb, q, vout, ps, cs, kB, y0, ny, true,
-                                 next_a);
-        } else {
-            next_a();
+        constexpr int EF = F, EG = 1 - F;
+        const int xF = EF == 0 ? q.xe : q.xo, xG = EG == 0 ? q.xe : q.xo;
+#pragma unroll
+        for (int jj = 1; jj < R - 1; jj += 2) {
+            pers_update<EF, R>(op, P, r, Ps, q, jj);
+#pragma unroll
+            for (int c = 0; c < 3; c++) Ps[q.at(jj, c, xF)] = P[c][EF][jj];
         }
         __syncthreads();
-        // the B plane above the next A plane into this step's B slot
-        if (more && kA + 3 <= nz) {
-            load_plane(W(iBc), kA + 3);
-            cp_async_commit();
+#pragma unroll
+        for (int jj = 1; jj < R - 1; jj += 2) {
+            pers_update<EG, R>(op, P, r, Ps, q, jj);
+#pragma unroll
+            for (int c = 0; c < 3; c++) Ps[q.at(jj, c, xG)] = P[c][EG][jj];
         }
-        const int oAp = iAp, oBc = iBc;
-        iAp = iA;
-        iA = oAp;
-        iBc = iBn;
-        iBn = oBc;
+        __syncthreads();
+#pragma unroll
+        for (int jj = 2; jj < R - 2; jj += 2) {
+            pers_update<EF, R>(op, P, r, Ps, q, jj);
+#pragma unroll
+            for (int c = 0; c < 3; c++) Ps[q.at(jj, c, xF)] = P[c][EF][jj];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int jj = 2; jj < R - 2; jj += 2) pers_update<EG, R>(op, P, r, Ps, q, jj);
+        float *Ok = vout + (long)T.k * ps;
+#pragma unroll
+        for (int jj = 1 + F; jj < TY + 1 + F; jj++) {
+            const int y = y0 - 1 - F + jj;
+            if (y < ny) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    Ok[c * cs + (long)y * nx + q.xe] = P[c][0][jj];
+                    Ok[c * cs + (long)y * nx + q.xo] = P[c][1][jj];
+                }
+            }
+        }
+        // every thread is done with this tile: publish an A tile, refill
+        __syncthreads();
+        if (T.ph == 0 && t == 0) st_release(sy.aflag + (long)s * (nsteps + 1) + T.m, want);
+        T = Tn;
+        if (T.r < NR) issue_bz(T, sL, sH, fp, fv);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -1071,22 +1050,23 @@ int g_fused_slots[64][kPersMaxNx / 64];
 
 inline int fused_nstrips(const Dims &d) { return (d.ny + kPersTY - 1) / kPersTY; }
 
-// runs along z per strip: as many as fit beside the other strips' runs with
-// all CTAs co-resident, at most one per step
-inline int fused_kz(const Dims &d, int slots) {
+// CTAs per strip: as many as fit beside the other strips' with all CTAs
+// co-resident, so that every chunk has at least one step
+inline int fused_k(const Dims &d, int slots) {
     const int nsteps = d.nz / 2, ns = fused_nstrips(d);
-    int kz = slots / ns;
-    return kz < 1 ? 0 : (kz > nsteps ? nsteps : kz);
+    int k = slots / ns;
+    const int kmax = nsteps / fused_rounds(nsteps);
+    return k < 1 || kmax < 1 ? 0 : (k > kmax ? kmax : k);
 }
 
 template <int F, bool SPLIT>
 cudaError_t launch_fused(const Dims &d, const FineRowsOp &op, const float *b, const float *vin,
-                         float *vout, int kA0, int kz, const SweepSync &sy, cudaStream_t s) {
+                         float *vout, int kA0, int K, const SweepSync &sy, cudaStream_t s) {
     const int nsteps = d.nz / 2, ns = fused_nstrips(d);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ns * kz);
+    cfg.gridDim = dim3(ns * K);
     cfg.blockDim = dim3(d.nx / 2);
-    cfg.dynamicSmemBytes = fused_floats(d.nx) * sizeof(float);
+    cfg.dynamicSmemBytes = pers_floats(d.nx) * sizeof(float);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -1094,7 +1074,7 @@ cudaError_t launch_fused(const Dims &d, const FineRowsOp &op, const float *b, co
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gs_rows_f<F, SPLIT>, d, op, b, vin, vout, kA0,
-                                             nsteps, ns, kz, sy);
+                                             nsteps, ns, K, sy);
     count_launch();
     return e;
 }
@@ -1140,7 +1120,7 @@ cudaError_t smoother_init() {
     SET((k_gs_rows_p<FineRowsOp, 0, true, true>), smem_p)
     SET((k_gs_rows_p<CoarseRowsOp, 0, false, false>), smem_p)
     SET((k_gs_rows_p<CoarseRowsOp, 1, false, false>), smem_p)
-    const int smem_f = (int)(fused_floats(kPersMaxNx) * sizeof(float));
+    const int smem_f = smem_p;
     SET((k_gs_rows_f<0, false>), smem_f)
     SET((k_gs_rows_f<0, true>), smem_f)
     SET((k_gs_rows_f<1, false>), smem_f)
@@ -1158,7 +1138,7 @@ cudaError_t smoother_init() {
             for (const void *kf : kerns) {
                 int nb = 0;
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &nb, kf, nx / 2, fused_floats(nx) * sizeof(float));
+                    &nb, kf, nx / 2, pers_floats(nx) * sizeof(float));
                 if (e != cudaSuccess) return e;
                 lo = nb < lo ? nb : lo;
             }
@@ -1167,16 +1147,12 @@ cudaError_t smoother_init() {
     return cudaSuccess;
 }
 
-bool fused_sweep_sizes(const Dims &d, long &naflag, long &npflag, long &nxbuf) {
+bool fused_sweep_sizes(const Dims &d, long &naflag) {
     int sms = 0, dev = 0;
     if (!rows_p_shape(d, sms) || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
         return false;
-    const int kz = fused_kz(d, g_fused_slots[dev][d.nx / 64 - 1]);
-    if (kz < 1) return false;
-    const long ns = fused_nstrips(d);
-    naflag = ns * (d.nz / 2 + 1);
-    npflag = ns * kz;
-    nxbuf = ns * kz * kPersTY * 3L * d.nx;
+    if (fused_k(d, g_fused_slots[dev][d.nx / 64 - 1]) < 1) return false;
+    naflag = (long)fused_nstrips(d) * (d.nz / 2 + 1);
     return true;
 }
 
@@ -1190,7 +1166,7 @@ cudaError_t gs_sweep_fine_rows(const Dims &d, const Fine<float> &f, const float 
         const FineRowsOp op{f};
         int dev = 0;
         const int kz = sync && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64
-                           ? fused_kz(d, g_fused_slots[dev][d.nx / 64 - 1])
+                           ? fused_k(d, g_fused_slots[dev][d.nx / 64 - 1])
                            : 0;
         if (kz > 0) {
             // ascending: A = even planes from 2 (colours 0-3, F = 0);
