@@ -100,6 +100,10 @@ def lib():
         L.ora_qs_step.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                   C.POINTER(STZ), C.POINTER(BC), C.c_double, _D, _D, _D,
                                   C.c_double, C.c_int, _I, _D]
+        L.ora_eno.argtypes = [_D, C.c_double, C.c_double]
+        L.ora_eno.restype = C.c_double
+        L.ora_explicit_step.argtypes = [C.c_int, C.c_int, C.c_int] + [C.c_double] * 6 + [
+            C.POINTER(STZ), C.POINTER(BC), C.c_double, _D, _D, _D]
     return _lib
 
 
@@ -267,3 +271,17 @@ def qs_step(mg: MG, v, sig, chi, h, dt, lam, mu, stz: STZ, bc: BC, t, tol=1e-10,
     st = lib().ora_qs_step(mg.h, h, dt, lam, mu, C.byref(stz), C.byref(bc), t, _p(v), _p(sig),
                            _p(chi), tol, max_cycles, C.byref(cyc), _p(hist))
     return st, cyc.value, hist[: cyc.value + 1].copy()
+
+
+def eno(f5, u, h) -> float:
+    """ENO first derivative of Eq. (33) from the 5 values at offsets -2..2."""
+    f = np.ascontiguousarray(f5, dtype=np.float64)
+    assert f.shape == (5,)
+    return lib().ora_eno(_p(f), float(u), float(h))
+
+
+def explicit_step(v, sig, chi, h, dt, rho, lam, mu, kappa, stz: STZ, bc: BC, t) -> None:
+    """One explicit forward-Euler step (section 3.2, Eqs. 24-26) in place."""
+    nx, ny, nz = _dims(v)
+    lib().ora_explicit_step(nx, ny, nz, h, dt, rho, lam, mu, kappa, C.byref(stz), C.byref(bc), t,
+                            _p(v), _p(sig), _p(chi))

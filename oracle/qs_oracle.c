@@ -32,7 +32,14 @@
  *   - chi diffusion is a conservative 7-point stencil with face-averaged
  *     D^pl; z ghost cells take linearly extrapolated sigma and chi (section 4)
  *     and D^pl evaluated from them;
- *   - the sign of tr(L) sigma is minus (Eqs. 1, 15, 27).
+ *   - the sign of tr(L) sigma is minus (Eqs. 1, 15, 27; also in the explicit
+ *     Eq. 25, whose plus is read as a typo);
+ *   - explicit method (section 3.2): the momentum balance Eq. (24) is read
+ *     as rho (v' - v)/dt = -rho (v.grad) v + div sigma + rho kappa lap v,
+ *     kappa a diffusivity (m^2/s; section 4 sets kappa = kappa' h and the
+ *     stability limit dt <= h^2 / (6 kappa)); sigma is advected with the mean
+ *     of its cell's corner velocities; ghost values two planes beyond a wall
+ *     reflect v through the wall value and extrapolate cell fields linearly.
  *
  * Stencil tables: S[d][a][b] with d = (dz+1)*9 + (dy+1)*3 + (dx+1) for
  * offsets in {-1,0,1}^3, a = output component, b = input component.
@@ -921,4 +928,192 @@ int ora_qs_step(ora_mg *m, double h, double dt, double lam, double mu, const ora
     free(chi_new);
     free(b);
     return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* explicit method (section 3.2, Eqs. 24-26; ENO advection, Eq. 33)    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * ENO first derivative along one line, Eq. (33): f[0..4] are the values at
+ * offsets -2..2 (spacing h) around the point and u the velocity component
+ * along the line there.  The one-sided three-point derivative on the
+ * upwind side is taken when the second derivative (Eq. 32) at the point
+ * exceeds in magnitude the one at the upwind neighbour; otherwise the
+ * centred difference.
+ */
+double ora_eno(const double *f, double u, double h)
+{
+    double fxx_m = (f[2] - 2.0 * f[1] + f[0]) / (h * h);
+    double fxx_0 = (f[3] - 2.0 * f[2] + f[1]) / (h * h);
+    double fxx_p = (f[4] - 2.0 * f[3] + f[2]) / (h * h);
+    if (u < 0.0 && fabs(fxx_0) > fabs(fxx_p))
+        return (-f[4] + 4.0 * f[3] - 3.0 * f[2]) / (2.0 * h);
+    if (u > 0.0 && fabs(fxx_0) > fabs(fxx_m))
+        return (3.0 * f[2] - 4.0 * f[1] + f[0]) / (2.0 * h);
+    return (f[3] - f[1]) / (2.0 * h);
+}
+
+/* corner value of component a at plane kk, which may lie up to two planes
+ * beyond a wall: there the field is reflected through the wall value
+ * (Dirichlet ghost, section 3.5): v(-m) = 2 v(0) - v(m) */
+static double corner_val(const double *v, int nx, int ny, int nz, int a, int kk, int j, int i)
+{
+    if (kk < 0)
+        return 2.0 * v[node(nx, ny, nz, a, 0, j, i)] - v[node(nx, ny, nz, a, -kk, j, i)];
+    if (kk > nz)
+        return 2.0 * v[node(nx, ny, nz, a, nz, j, i)] - v[node(nx, ny, nz, a, 2 * nz - kk, j, i)];
+    return v[node(nx, ny, nz, a, kk, j, i)];
+}
+
+/* cell value of the scalar field f at layer kk, which may lie up to two
+ * layers beyond the z boundary: there the field is extrapolated linearly
+ * from the two nearest layers (free boundary ghost, section 3.5) */
+static double cell_val(const double *f, int nx, int ny, int nz, int kk, int j, int i)
+{
+    if (kk < 0)
+        return f[cell(nx, ny, 0, j, i)] + kk * (f[cell(nx, ny, 1, j, i)] - f[cell(nx, ny, 0, j, i)]);
+    if (kk > nz - 1)
+        return f[cell(nx, ny, nz - 1, j, i)] +
+               (kk - (nz - 1)) * (f[cell(nx, ny, nz - 1, j, i)] - f[cell(nx, ny, nz - 2, j, i)]);
+    return f[cell(nx, ny, kk, j, i)];
+}
+
+/*
+ * One explicit forward-Euler step (section 3.2) from t to t + dt, in place,
+ * every right-hand side from the state at t:
+ *   sigma: Eq. (25), -(u.grad) sigma + L sigma + sigma L^T - tr(L) sigma
+ *          + C:(D - D^pl sigma0 / sbar), at cell centres; L and D from the
+ *          Eq. (31) gradient of v; u the mean of the cell's 8 corner
+ *          velocities; the advection by ENO (Eq. 33) along x, y, z;
+ *   chi:   Eq. (26), as in the quasi-static step;
+ *   v:     Eq. (24) at interior corners, rho (v' - v)/dt = -rho (v.grad) v
+ *          + div sigma + rho kappa lap v, with the corner divergence of
+ *          Eq. (31), the Laplacian of Eq. (32) and ENO advection;
+ *   walls at t + dt (Eqs. 37-38, 48-49).
+ * kappa is the damping diffusivity (m^2/s), kappa = kappa' h in section 4.
+ */
+void ora_explicit_step(int nx, int ny, int nz, double h, double dt, double rho, double lam,
+                       double mu, double kappa, const ora_stz *p, const ora_bc *bc, double t,
+                       double *v, double *sig, double *chi)
+{
+    static const int comp[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    long nc = (long)nx * ny * nz, nn = 3L * (nz + 1) * ny * nx;
+    double *v0 = (double *)malloc(nn * sizeof(double));
+    double *s0 = (double *)malloc(6 * nc * sizeof(double));
+    double *dpl = (double *)malloc(nc * sizeof(double));
+    double *sbar = (double *)malloc(nc * sizeof(double));
+    double *chi_new = (double *)malloc(nc * sizeof(double));
+    memcpy(v0, v, nn * sizeof(double));
+    memcpy(s0, sig, 6 * nc * sizeof(double));
+
+    /* stress, Eq. (25) */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long q = cell(nx, ny, k, j, i);
+                double s6[6], s[3][3], L[3][3], u[3] = {0.0, 0.0, 0.0};
+                for (int c = 0; c < 6; c++)
+                    s6[c] = s0[c * nc + q];
+                sym_full(s6, s);
+                cell_grad(nx, ny, nz, v0, h, k, j, i, L);
+                for (int a = 0; a < 3; a++)
+                    for (int dk = 0; dk < 2; dk++)
+                        for (int dj = 0; dj < 2; dj++)
+                            for (int di = 0; di < 2; di++)
+                                u[a] += 0.125 * v0[node(nx, ny, nz, a, k + dk, wrap(j + dj, ny),
+                                                        wrap(i + di, nx))];
+                double sb = sbar_of(s);
+                double D = ora_dpl(p, sb, chi[q]);
+                dpl[q] = D;
+                sbar[q] = sb;
+                double adv[6];
+                for (int c = 0; c < 6; c++) {
+                    const double *f = s0 + c * nc;
+                    double fx[5], fy[5], fz[5];
+                    for (int m = -2; m <= 2; m++) {
+                        fx[m + 2] = f[cell(nx, ny, k, j, wrap(i + m, nx))];
+                        fy[m + 2] = f[cell(nx, ny, k, wrap(j + m, ny), i)];
+                        fz[m + 2] = cell_val(f, nx, ny, nz, k + m, j, i);
+                    }
+                    adv[c] = u[0] * ora_eno(fx, u[0], h) + u[1] * ora_eno(fy, u[1], h) +
+                             u[2] * ora_eno(fz, u[2], h);
+                }
+                double trL = L[0][0] + L[1][1] + L[2][2];
+                double tr3 = (s[0][0] + s[1][1] + s[2][2]) / 3.0;
+                double rate[3][3];
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++) {
+                        double r = -adv[comp[a][b]] - trL * s[a][b];
+                        for (int c = 0; c < 3; c++)
+                            r += L[a][c] * s[c][b] + s[a][c] * L[b][c];
+                        /* C:D with D = (L + L^T)/2 */
+                        r += (a == b ? lam * trL : 0.0) + mu * (L[a][b] + L[b][a]);
+                        if (D > 0.0)
+                            r -= 2.0 * mu * D * (s[a][b] - (a == b ? tr3 : 0.0)) / sb;
+                        rate[a][b] = r;
+                    }
+                sig[0 * nc + q] = s[0][0] + dt * rate[0][0];
+                sig[1 * nc + q] = s[1][1] + dt * rate[1][1];
+                sig[2 * nc + q] = s[2][2] + dt * rate[2][2];
+                sig[3 * nc + q] = s[1][2] + dt * rate[1][2];
+                sig[4 * nc + q] = s[0][2] + dt * rate[0][2];
+                sig[5 * nc + q] = s[0][1] + dt * rate[0][1];
+            }
+
+    /* effective temperature, Eq. (26), from the state at t */
+    ora_chi_update(nx, ny, nz, h, dt, p, s0, chi, dpl, sbar, chi_new);
+    memcpy(chi, chi_new, nc * sizeof(double));
+
+    /* velocity, Eq. (24), at interior corners */
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                int im = wrap(i - 1, nx), jm = wrap(j - 1, ny);
+                int is[2] = {im, i}, js[2] = {jm, j}, ks[2] = {k - 1, k};
+                double u[3];
+                for (int a = 0; a < 3; a++)
+                    u[a] = v0[node(nx, ny, nz, a, k, j, i)];
+                for (int a = 0; a < 3; a++) {
+                    /* corner divergence of sigma (Eq. 31 shifted by -1/2) */
+                    const double *fx = s0 + comp[a][0] * nc;
+                    const double *fy = s0 + comp[a][1] * nc;
+                    const double *fz = s0 + comp[a][2] * nc;
+                    double div = 0.0;
+                    for (int e = 0; e < 2; e++)
+                        for (int w = 0; w < 2; w++) {
+                            div += fx[cell(nx, ny, ks[w], js[e], i)] - fx[cell(nx, ny, ks[w], js[e], im)];
+                            div += fy[cell(nx, ny, ks[w], j, is[e])] - fy[cell(nx, ny, ks[w], jm, is[e])];
+                            div += fz[cell(nx, ny, k, js[w], is[e])] - fz[cell(nx, ny, k - 1, js[w], is[e])];
+                        }
+                    div /= 4.0 * h;
+                    /* Laplacian, Eq. (32) in x, y and z */
+                    double c0 = u[a];
+                    double lap = (v0[node(nx, ny, nz, a, k, j, wrap(i + 1, nx))] - 2.0 * c0 +
+                                  v0[node(nx, ny, nz, a, k, j, im)]) +
+                                 (v0[node(nx, ny, nz, a, k, wrap(j + 1, ny), i)] - 2.0 * c0 +
+                                  v0[node(nx, ny, nz, a, k, jm, i)]) +
+                                 (v0[node(nx, ny, nz, a, k + 1, j, i)] - 2.0 * c0 +
+                                  v0[node(nx, ny, nz, a, k - 1, j, i)]);
+                    lap /= h * h;
+                    /* ENO advection (Eq. 33) */
+                    double fxl[5], fyl[5], fzl[5];
+                    for (int m = -2; m <= 2; m++) {
+                        fxl[m + 2] = v0[node(nx, ny, nz, a, k, j, wrap(i + m, nx))];
+                        fyl[m + 2] = v0[node(nx, ny, nz, a, k, wrap(j + m, ny), i)];
+                        fzl[m + 2] = corner_val(v0, nx, ny, nz, a, k + m, j, i);
+                    }
+                    double adv = u[0] * ora_eno(fxl, u[0], h) + u[1] * ora_eno(fyl, u[1], h) +
+                                 u[2] * ora_eno(fzl, u[2], h);
+                    v[node(nx, ny, nz, a, k, j, i)] = c0 + dt * (-adv + div / rho + kappa * lap);
+                }
+            }
+    ora_wall_fill(nx, ny, nz, h, bc, t + dt, v);
+    free(v0);
+    free(s0);
+    free(dpl);
+    free(sbar);
+    free(chi_new);
 }
