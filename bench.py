@@ -28,6 +28,7 @@ error against the FP64 run.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -81,6 +82,13 @@ def parse():
     ap.add_argument("--grad", action="store_true",
                     help="64^3 x 40 FP64 steps: plastic work forward alone and with dW/dchi0")
     ap.add_argument("--every", type=int, default=8, help="--grad: checkpoint interval")
+    ap.add_argument("--explicit", action="store_true",
+                    help="explicit method against the quasi-static one on the section-4 "
+                         "comparison geometry (64 x 64 x 32)")
+    ap.add_argument("--zeta", default="1e4", help="--explicit: comma-separated zeta values")
+    ap.add_argument("--t-end", type=float, default=20.0, help="--explicit: end time in t_s")
+    ap.add_argument("--fma-peak", action="store_true",
+                    help="measure the FP64 and FP32 FMA rate of the GPU (the FP64 kernels' roofline)")
     return ap.parse_args()
 
 
@@ -460,14 +468,13 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    cyc = outer = 0
-    worst = 0.0
-    for _ in range(K):
-        st, s = ctx.step(state, w.dt, TOL)
-        cyc += s.cycles
-        outer += s.outer_iters
-        worst = max(worst, s.rel_resid)
+    # the K steps in one qs_run call (each step's stress correction fused
+    # with the next step's predictor)
+    _, run_stats = ctx.run(state, K, w.dt, TOL)
     ev1.record(stream)
+    cyc = sum(s.cycles for s in run_stats)
+    outer = sum(s.outer_iters for s in run_stats)
+    worst = max(s.rel_resid for s in run_stats)
     torch.cuda.synchronize()
     launches = binding.launch_count() - l0
     clk = clocks.stop()
@@ -747,6 +754,88 @@ def run_cpu_report(args):
     return out
 
 
+def run_explicit(args):
+    """The explicit method (section 3.2) against the quasi-static method on the
+    comparison geometry of section 4: 64 x 64 x 32 cells (h = L/32, height L),
+    simple shear, chi0 the cylindrical inclusion 600 K + 200 K
+    exp(-500 (y^2 + z^2) / L^2) for |x| < L/2 (600 K elsewhere), sigma0 = 0,
+    v0 = 0; the STZ time scale tau0 / zeta and wall speed 1e-7 zeta L / t_s;
+    explicit steps dt_e <= t_s h^2 / (20 L^2) (the largest that divides the
+    quasi-static step) with damping kappa = 4.8 (L / t_s) h; quasi-static steps
+    of 100 t_s / zeta (mixed precision to 1e-10).  Reported: the explicit
+    step's device time, and at intervals the root-mean-square differences
+    (over cells, or corners for v) of chi, sigma and v between the two runs,
+    normalised by chi_inf, s_Y and the wall speed."""
+    import torch
+
+    from paper_1904_03808_gb300 import MG_FP64, MG_MIXED, Context, make_state
+    from paper_1904_03808_gb300 import inputs as I
+    n, nz = 64, 32
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    out = {"mode": "explicit", "grid": [n, n, nz], "t_end_ts": args.t_end, "runs": []}
+    for zeta in (float(z) for z in args.zeta.split(",")):
+        w = I.Workload(n, steps=1, nz=nz, seed=1)
+        L, h, ts = w.L, w.h, w.ts
+        w.U_B = 1e-7 * zeta * L / ts
+        stz = dict(w.stz)
+        stz["tau0"] = stz["tau0"] / zeta
+        x = -L + (np.arange(n) + 0.5) * h
+        z = -0.5 * nz * h + (np.arange(nz) + 0.5) * h
+        Z, Y, X = np.meshgrid(z, x, x, indexing="ij")
+        chi0 = np.where(np.abs(X) < L / 2, 600.0 + 200.0 * np.exp(-500.0 * (Y * Y + Z * Z) / (L * L)),
+                        600.0)
+        v0 = np.zeros((3, nz + 1, n, n))
+        s0 = np.zeros((6, nz, n, n))
+        dt_qs = 100.0 * ts / zeta
+        ne = int(math.ceil(dt_qs / (ts * h * h / (20.0 * L * L))))
+        dt_e = dt_qs / ne
+        kappa = 4.8 * L / ts * h
+        runs = {}
+        for name, prec in (("explicit", MG_FP64), ("qs", MG_MIXED)):
+            ctx = Context(n, n, nz, h, I.TABLE1["K"], w.mu, bc=w.bc_values(), stz=stz,
+                          precision=prec, max_cycles=100, stream=stream)
+            ts_ = [torch.from_numpy(a.copy()).to(dev) for a in (v0, s0, chi0)]
+            runs[name] = (ctx, ts_, make_state(*ts_, 0.0))
+        nq = int(round(args.t_end * ts / dt_qs))
+        every = max(1, nq // 20)
+        rows, e_ms, q_ms = [], [], []
+        for m in range(nq):
+            for name in ("qs", "explicit"):
+                ctx, _, st = runs[name]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if name == "qs":
+                    ctx.step(st, dt_qs, TOL)
+                else:
+                    ctx.explicit_step(st, dt_e, I.TABLE1["rho"], kappa, nsteps=ne)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                (q_ms if name == "qs" else e_ms).append(e0.elapsed_time(e1))
+            if (m + 1) % every == 0 or m + 1 == nq:
+                (vq, sq, cq), (ve, se, ce) = runs["qs"][1], runs["explicit"][1]
+                rms = lambda d: float(torch.sqrt((d * d).sum(0).mean()))  # noqa: E731
+                dsig = sq - se
+                # Frobenius norm: off-diagonal components count twice
+                fro = torch.sqrt((dsig[:3] ** 2).sum(0) + 2.0 * (dsig[3:] ** 2).sum(0))
+                rows.append({"t_ts": float("%.4g" % ((m + 1) * dt_qs / ts)),
+                             "chi": float("%.3g" % (rms((cq - ce)[None]) / w.stz["chi_inf"])),
+                             "sigma": float("%.3g" % (float(torch.sqrt((fro * fro).mean())) /
+                                                      w.stz["sY"])),
+                             "v": float("%.3g" % (rms(vq - ve) / w.U_B)),
+                             "chi_max_qs": float("%.4g" % float(cq.max()))})
+        for ctx, _, _ in runs.values():
+            ctx.close()
+        out["runs"].append({"zeta": zeta, "dt_qs_ts": dt_qs / ts, "dt_e_ts": dt_e / ts,
+                            "explicit_steps": ne * nq, "kappa_m2_s": kappa,
+                            "explicit_ms_per_step": statistics.mean(e_ms[1:] or e_ms) / ne,
+                            "qs_ms_per_step": statistics.mean(q_ms[1:] or q_ms),
+                            "differences": rows})
+    out["note"] = ("differences: root-mean-square over the grid of chi_qs - chi_e (/chi_inf), the "
+                   "Frobenius norm of sigma_qs - sigma_e (/s_Y) and |v_qs - v_e| (/U_B)")
+    return out
+
+
 def run_grad(args):
     """The differentiation workload: 64^3 cells, 40 FP64 steps of simple
     shear from the STZ-active preload; the plastic work W alone
@@ -794,6 +883,36 @@ def run_grad(args):
     return out
 
 
+def run_fma_peak(args):
+    """FP64 and FP32 fused multiply-add rates (csrc/peak_probe.cu, its own
+    library), with the SM clocks sampled while they run."""
+    import ctypes
+    import torch
+    from paper_1904_03808_gb300 import build as B
+    B.build()
+    torch.cuda.init()
+    L = ctypes.CDLL(B.PROBE_LIB)
+    L.qsmg_fma_peak.restype = ctypes.c_int
+    L.qsmg_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    out = {"mode": "fma-peak", "kernel": "CTAs of 256 threads, 16 independent FMA chains a thread",
+           "gpu": torch.cuda.get_device_name(0), "sms": torch.cuda.get_device_properties(0).multi_processor_count}
+    for name, fp64, iters in (("fp64", 1, 20000), ("fp32", 0, 200000)):
+        rows = []
+        clocks = Clocks(0)
+        clocks.start()
+        for bpsm in (4, 8):
+            tf, ms = ctypes.c_double(), ctypes.c_double()
+            st = L.qsmg_fma_peak(fp64, bpsm, iters, 5, ctypes.byref(tf), ctypes.byref(ms))
+            if st != 0:
+                raise RuntimeError("qsmg_fma_peak failed with %d" % st)
+            rows.append({"blocks_per_sm": bpsm, "tflops": tf.value, "ms": ms.value})
+        out[name] = {"tflops": max(r["tflops"] for r in rows), "runs": rows,
+                     "clocks": clocks.stop()}
+    out["fp32_over_fp64"] = out["fp32"]["tflops"] / out["fp64"]["tflops"]
+    return out
+
+
 def main():
     args = parse()
     if args.sweep_only:
@@ -804,6 +923,10 @@ def main():
         out = run_cpu_report(args)
     elif args.grad:
         out = run_grad(args)
+    elif args.explicit:
+        out = run_explicit(args)
+    elif args.fma_peak:
+        out = run_fma_peak(args)
     elif args.disc:
         out = run_disc(args)
     else:

@@ -188,6 +188,23 @@ mg_status mg_solve(mg_ctx *ctx, const double *rhs, double *v, double tol, mg_sta
  */
 mg_status qs_step(mg_ctx *ctx, qs_state *state, double dt, double tol, mg_stats *stats);
 
+/*
+ * qs_run -- nsteps quasi-static projection steps (section 3.3) of size dt,
+ * in place: the same arithmetic as nsteps calls of qs_step, with the stress
+ * correction of each step (Eq. 29) and the predictor of the next (Eq. 27)
+ * done in one pass over the cells, since both take the Eq. (31) gradient of
+ * the same velocity v^{n+1}.  Between the calls' steps nothing is observable,
+ * so the state is only complete on return.  qs_step is qs_run with nsteps = 1.
+ *   stats: NULL, or an array of nsteps entries that receives each step's
+ *          solve statistics.
+ *   nsteps = 0 leaves the state untouched and returns MG_OK.
+ * Errors as qs_step.  On MG_ERR_NOCONV or MG_ERR_NONFINITE the run stops
+ * after the step whose solve failed, with that step completed from the last
+ * iterate; state->step and state->t count the steps taken.
+ */
+mg_status qs_run(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
+                 mg_stats *stats);
+
 /* Release every buffer of the context (NULL is a no-op). */
 void mg_free(mg_ctx *ctx);
 
@@ -335,6 +352,34 @@ mg_status qs_plastic_work_backward(mg_ctx *ctx, const double *checkpoints, doubl
 mg_status qs_plastic_work_grad(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
                                int checkpoint_every, double *chibar, double *work,
                                mg_stats *stats);
+
+/*
+ * qs_explicit_step -- nsteps steps of the explicit method of section 3.2,
+ * the forward-Euler comparison scheme of the paper (no projection; the
+ * time step is limited by the elastic wave speed and by the damping,
+ * dt <= h^2 / (6 kappa)).  Each step, from the state at t:
+ *   stress (Eq. 25): sigma += dt (-(u.grad) sigma + L sigma + sigma L^T
+ *     - tr(L) sigma + C:(D - D^pl sigma0 / sbar)), L and D from the Eq. (31)
+ *     gradient of v, u the mean of a cell's 8 corner velocities;
+ *   chi (Eq. 26), as in qs_step;
+ *   velocity (Eq. 24) at interior corners: v += dt (-(v.grad) v
+ *     + div sigma / rho + kappa lap v), the corner divergence of Eq. (31)
+ *     and the Laplacian of Eq. (32);
+ *   the advection terms by the ENO derivative of Eq. (33), its stencils
+ *   reaching two points out; beyond the walls v is reflected through the
+ *   wall value and the cell fields are extrapolated linearly;
+ *   walls set at t + dt; state->t += dt, state->step += 1.
+ * The printed Eq. (24) carries neither rho on the advection term nor on the
+ * damping; here both are read as terms of rho dv/dt, with kappa a
+ * diffusivity (m^2/s), as the paper's kappa = kappa' h and its stability
+ * limit imply.
+ *   rho: density (kg/m^3); kappa: damping diffusivity (m^2/s), >= 0.
+ * Uses the context's moduli, STZ parameters and walls; allocates nothing.
+ * Errors: MG_ERR_ARG (null arrays, dt <= 0, rho <= 0, kappa < 0,
+ * nsteps < 0, context without stz/bc), MG_ERR_CUDA, MG_ERR_STATE.
+ */
+mg_status qs_explicit_step(mg_ctx *ctx, qs_state *state, double dt, double rho, double kappa,
+                           int nsteps);
 
 /* ------------------------------------------------------------------ */
 /* Measurement hooks                                                   */

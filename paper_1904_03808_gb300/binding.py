@@ -72,6 +72,8 @@ _SIGS = {
                            C.POINTER(stz_params), C.POINTER(mg_opts), _P, C.POINTER(_P)]),
     "mg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.POINTER(mg_stats)]),
     "qs_step": (C.c_int, [_P, C.POINTER(qs_state), C.c_double, C.c_double, C.POINTER(mg_stats)]),
+    "qs_run": (C.c_int, [_P, C.POINTER(qs_state), C.c_int, C.c_double, C.c_double,
+                         C.POINTER(mg_stats)]),
     "mg_free": (None, [_P]),
     "mg_status_str": (C.c_char_p, [C.c_int]),
     "mg_last_error": (C.c_char_p, []),
@@ -97,6 +99,8 @@ _SIGS = {
                                   C.c_int, _P, C.POINTER(C.c_double), C.POINTER(mg_stats)]),
     "qs_plastic_work_backward": (C.c_int, [_P, _P, C.c_double, C.c_long, C.c_int, C.c_double,
                                            C.c_double, C.c_int, _P, C.POINTER(mg_stats)]),
+    "qs_explicit_step": (C.c_int, [_P, C.POINTER(qs_state), C.c_double, C.c_double, C.c_double,
+                                   C.c_int]),
     "mg_profile": (C.c_int, [_P, C.c_int]),
     "mg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_long),
                                   C.POINTER(C.c_long)]),
@@ -220,6 +224,23 @@ class Context:
         if raise_on_error:
             _check(st, "qs_step")
         return st, s
+
+    def run(self, state: qs_state, nsteps, dt, tol=1e-10, raise_on_error=True):
+        """qs_run: nsteps projection steps in one call; returns (status, list
+        of each step's mg_stats)."""
+        n = int(nsteps)
+        arr = (mg_stats * max(n, 1))()
+        st = lib().qs_run(self.h, C.byref(state), n, dt, tol, arr)
+        if raise_on_error:
+            _check(st, "qs_run")
+        return st, [arr[i] for i in range(n)]
+
+    def explicit_step(self, state: qs_state, dt, rho, kappa, nsteps=1, raise_on_error=True):
+        """qs_explicit_step: nsteps steps of the explicit method (section 3.2)."""
+        st = lib().qs_explicit_step(self.h, C.byref(state), dt, rho, kappa, int(nsteps))
+        if raise_on_error:
+            _check(st, "qs_explicit_step")
+        return st
 
     def step_adjoint(self, state: qs_state, dt, vbar, sigbar, chibar, tol=1e-10, work_weight=1.0,
                      raise_on_error=True):

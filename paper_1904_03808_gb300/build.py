@@ -1,7 +1,9 @@
 """Build the sm_103a shared library ``_build/libqsmg.so`` with nvcc.
 
 The translation units are compiled in parallel (one -gencode, static cudart)
-and linked into one C-ABI shared library; nothing here needs a GPU.
+and linked into one C-ABI shared library; nothing here needs a GPU.  The
+FMA-rate probe (``csrc/peak_probe.cu``, a measurement aid) is built beside it
+as ``_build/libqsmg_peak.so``.
 """
 from __future__ import annotations
 
@@ -15,6 +17,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqsmg.so")
 SOURCES = ["mg_kernels.cu", "smoother_fast.cu", "smoother_rows.cu", "step_kernels.cu",
            "qsmg_host.cu", "static_scratch.cu"]
+PROBE = "peak_probe.cu"
+PROBE_LIB = os.path.join(OUT_DIR, "libqsmg_peak.so")
 HEADERS = ["qsmg_impl.h", os.path.join("..", "..", "include", "qsmg.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -44,6 +48,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if force or _stale(o, [s] + hdrs):
             cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o]
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    probe_src = os.path.join(CSRC, PROBE)
+    if force or _stale(PROBE_LIB, [probe_src]):
+        cmd = [nvcc, *ARCH, *FLAGS, "-shared", probe_src, "-o", PROBE_LIB]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for cmd, p in procs:
         out, _ = p.communicate()

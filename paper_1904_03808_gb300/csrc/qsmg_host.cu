@@ -1013,29 +1013,79 @@ mg_status mg_solve(mg_ctx *ctx, const double *rhs, double *v, double tol, mg_sta
     return solve_mixed(ctx, rhs, v, tol, st);
 }
 
-mg_status qs_step(mg_ctx *ctx, qs_state *state, double dt, double tol, mg_stats *stats) {
+mg_status qs_run(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol,
+                 mg_stats *stats) {
     CKS(check_ctx(ctx));
-    if (!state || !state->v || !state->sigma || !state->chi || !(dt > 0.0)) {
-        set_err("qs_step: null state array or dt <= 0");
+    if (!state || !state->v || !state->sigma || !state->chi || !(dt > 0.0) || nsteps < 0) {
+        set_err("qs_run: null state array, dt <= 0 or nsteps < 0");
         return MG_ERR_ARG;
     }
     if (!ctx->has_stz || !ctx->has_bc) {
-        set_err("qs_step: context was set up without stz/bc parameters");
+        set_err("qs_run: context was set up without stz/bc parameters");
         return MG_ERR_ARG;
     }
+    if (nsteps == 0) return MG_OK;
     const StepParams p = step_params(ctx, dt);
     CK(stress_predict(p, state->v, state->sigma, state->chi, ctx->sig_star, ctx->dpl, ctx->sbar,
                       ctx->st));
-    CK(chi_update(p, state->sigma, state->chi, ctx->dpl, ctx->sbar, ctx->chi_tmp, ctx->st));
-    CK(wall_fill(wall_params(ctx, state->t + dt), state->v, ctx->st));
-    CK(div_rhs(p, ctx->sig_star, ctx->rhs, ctx->st));
-    const mg_status s = mg_solve(ctx, ctx->rhs, state->v, tol, stats);
-    if (s == MG_ERR_CUDA || s == MG_ERR_STATE || s == MG_ERR_ARG) return s;
+    mg_status s = MG_OK;
+    for (int n = 0; n < nsteps; n++) {
+        // the previous step's correction and this step's predictor share v
+        if (n > 0)
+            CK(correct_predict(p, state->v, ctx->sig_star, state->sigma, ctx->chi_tmp, state->chi,
+                               ctx->dpl, ctx->sbar, ctx->st));
+        CK(chi_update(p, state->sigma, state->chi, ctx->dpl, ctx->sbar, ctx->chi_tmp, ctx->st));
+        CK(wall_fill(wall_params(ctx, state->t + dt), state->v, ctx->st));
+        CK(div_rhs(p, ctx->sig_star, ctx->rhs, ctx->st));
+        s = mg_solve(ctx, ctx->rhs, state->v, tol, stats ? stats + n : nullptr);
+        if (s == MG_ERR_CUDA || s == MG_ERR_STATE || s == MG_ERR_ARG) return s;
+        state->t += dt;
+        state->step += 1;
+        if (s != MG_OK) break;  // advance this step with the last iterate, then stop
+    }
     CK(stress_correct(p, state->v, ctx->sig_star, state->sigma, ctx->chi_tmp, state->chi, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    state->t += dt;
-    state->step += 1;
     return s;
+}
+
+mg_status qs_step(mg_ctx *ctx, qs_state *state, double dt, double tol, mg_stats *stats) {
+    return qs_run(ctx, state, 1, dt, tol, stats);
+}
+
+mg_status qs_explicit_step(mg_ctx *ctx, qs_state *state, double dt, double rho, double kappa,
+                           int nsteps) {
+    CKS(check_ctx(ctx));
+    if (!state || !state->v || !state->sigma || !state->chi || !(dt > 0.0) || !(rho > 0.0) ||
+        !(kappa >= 0.0) || nsteps < 0) {
+        set_err("qs_explicit_step: null state array, dt <= 0, rho <= 0, kappa < 0 or nsteps < 0");
+        return MG_ERR_ARG;
+    }
+    if (!ctx->has_stz || !ctx->has_bc) {
+        set_err("qs_explicit_step: context was set up without stz/bc parameters");
+        return MG_ERR_ARG;
+    }
+    const Dims &d = ctx->L[0];
+    const size_t nc = (size_t)d.nx * d.ny * d.nz, nv = corner_count(d);
+    const StepParams p = step_params(ctx, dt);
+    // the new stress, chi and velocity go to the context's step scratch
+    // (sig_star, chi_tmp, rhs), then back into the state
+    for (int n = 0; n < nsteps; n++) {
+        CK(explicit_stress(p, state->v, state->sigma, state->chi, ctx->sig_star, ctx->dpl,
+                           ctx->sbar, ctx->st));
+        CK(chi_update(p, state->sigma, state->chi, ctx->dpl, ctx->sbar, ctx->chi_tmp, ctx->st));
+        CK(explicit_velocity(p, rho, kappa, state->v, state->sigma, ctx->rhs, ctx->st));
+        CK(cudaMemcpyAsync(state->sigma, ctx->sig_star, 6 * nc * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemcpyAsync(state->chi, ctx->chi_tmp, nc * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemcpyAsync(state->v, ctx->rhs, nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->st));
+        CK(wall_fill(wall_params(ctx, state->t + dt), state->v, ctx->st));
+        state->t += dt;
+        state->step += 1;
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
 }
 
 // ------------------------------------------------------------ components

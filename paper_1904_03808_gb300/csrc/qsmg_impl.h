@@ -230,7 +230,21 @@ cudaError_t div_rhs(const StepParams &p, const double *sig_star, double *b, cuda
 // sigma = sigma* + dt C:D(v); if chi_src is given also chi_dst = chi_src
 cudaError_t stress_correct(const StepParams &p, const double *v, const double *sig_star,
                            double *sig, const double *chi_src, double *chi_dst, cudaStream_t s);
+// Eq. (29) of one step fused with Eq. (27) of the next (same v): sig_star is
+// sigma* of the finished step on entry, of the next step on return
+cudaError_t correct_predict(const StepParams &p, const double *v, double *sig_star, double *sig,
+                            const double *chi_src, double *chi_dst, double *dpl, double *sbar,
+                            cudaStream_t s);
 cudaError_t wall_fill(const WallParams &w, double *v, cudaStream_t s);
+// explicit method (section 3.2), one forward-Euler step from the state
+// (v, sig, chi): the stress of Eq. (25) into sig_new with D^pl and sbar of
+// the state, and the velocity of Eq. (24) at the interior corners into v_new
+// (rho the density, kappa the damping diffusivity)
+cudaError_t explicit_stress(const StepParams &p, const double *v, const double *sig,
+                            const double *chi, double *sig_new, double *dpl, double *sbar,
+                            cudaStream_t s);
+cudaError_t explicit_velocity(const StepParams &p, double rho, double kappa, const double *v,
+                              const double *sig, double *v_new, cudaStream_t s);
 
 // ---------------------------------------------------------------- adjoint
 // (transposes of the step's equations; stored stress adjoints, see

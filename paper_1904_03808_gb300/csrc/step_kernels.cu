@@ -116,28 +116,20 @@ __device__ __forceinline__ bool cell_column(int nx, int ny, int nz, CellColumn &
     return true;
 }
 
-// Eq. (27): sigma* = sigma + dt (L sigma + sigma L^T - tr(L) sigma - 2 mu D^pl sigma0 / sbar)
-__global__ void k_stress_predict(StepParams p, StzConst c, const double *__restrict__ v,
-                                 const double *__restrict__ sig, const double *__restrict__ chi,
-                                 double *__restrict__ sig_star, double *__restrict__ dpl,
-                                 double *__restrict__ sbar_out, long nc) {
-    CellColumn C;
-    if (!cell_column(p.nx, p.ny, p.nz, C)) return;
-    GradPlane lo = grad_plane(v, C.cs, C.k0 * C.pl, C.r0, C.r1, C.i, C.i1);
-    for (int k = C.k0; k < C.k1; k++) {
-    const GradPlane hi = grad_plane(v, C.cs, (k + 1) * C.pl, C.r0, C.r1, C.i, C.i1);
-    const long q = k * C.pl + C.r0 + C.i;
-    double G[3][3];
-    grad_cell(lo, hi, 0.25 / p.h, G);
-    lo = hi;
-    double s6[6];
-#pragma unroll
-    for (int a = 0; a < 6; a++) s6[a] = sig[a * nc + q];
+// Eq. (27) at cell q: sigma* = sigma + dt (L sigma + sigma L^T - tr(L) sigma
+// - 2 mu D^pl sigma0 / sbar) from the cell-centre gradient G of v^n and the
+// cell's sigma^n (s6) and chi^n; also stores D^pl and sbar
+__device__ __forceinline__ void predict_cell(const StepParams &p, const StzConst &c,
+                                             const double (&G)[3][3], const double (&s6)[6],
+                                             double chi_q, long q, long nc,
+                                             double *__restrict__ sig_star,
+                                             double *__restrict__ dpl,
+                                             double *__restrict__ sbar_out) {
     // full symmetric matrix
     const double S[3][3] = {{s6[0], s6[5], s6[4]}, {s6[5], s6[1], s6[3]}, {s6[4], s6[3], s6[2]}};
     const double sb = sbar_of(s6);
     const double inv_sb = sb > 0.0 ? 1.0 / sb : 0.0;
-    const double D = stz_rate(c, sb, inv_sb, chi[q]);
+    const double D = stz_rate(c, sb, inv_sb, chi_q);
     const double trL = G[0][0] + G[1][1] + G[2][2];
     const double m = (s6[0] + s6[1] + s6[2]) * (1.0 / 3.0);
     const double pl = (D > 0.0) ? 2.0 * p.mu * D * inv_sb : 0.0;
@@ -154,6 +146,39 @@ __global__ void k_stress_predict(StepParams p, StzConst c, const double *__restr
     }
     dpl[q] = D;
     sbar_out[q] = sb;
+}
+
+// Eq. (29) at one cell: sigma = sigma* + dt (lam tr(D) I + 2 mu D), D = sym G
+__device__ __forceinline__ void correct_cell(const StepParams &p, const double (&G)[3][3],
+                                             const double (&ss)[6], double (&s6)[6]) {
+    const double tr = G[0][0] + G[1][1] + G[2][2];
+    const double dt = p.dt, lam = p.lam, mu = p.mu;
+    s6[0] = ss[0] + dt * (lam * tr + 2.0 * mu * G[0][0]);
+    s6[1] = ss[1] + dt * (lam * tr + 2.0 * mu * G[1][1]);
+    s6[2] = ss[2] + dt * (lam * tr + 2.0 * mu * G[2][2]);
+    s6[3] = ss[3] + dt * mu * (G[1][2] + G[2][1]);
+    s6[4] = ss[4] + dt * mu * (G[0][2] + G[2][0]);
+    s6[5] = ss[5] + dt * mu * (G[0][1] + G[1][0]);
+}
+
+// Eq. (27) over a column chunk of cells
+__global__ void k_stress_predict(StepParams p, StzConst c, const double *__restrict__ v,
+                                 const double *__restrict__ sig, const double *__restrict__ chi,
+                                 double *__restrict__ sig_star, double *__restrict__ dpl,
+                                 double *__restrict__ sbar_out, long nc) {
+    CellColumn C;
+    if (!cell_column(p.nx, p.ny, p.nz, C)) return;
+    GradPlane lo = grad_plane(v, C.cs, C.k0 * C.pl, C.r0, C.r1, C.i, C.i1);
+    for (int k = C.k0; k < C.k1; k++) {
+        const GradPlane hi = grad_plane(v, C.cs, (k + 1) * C.pl, C.r0, C.r1, C.i, C.i1);
+        const long q = k * C.pl + C.r0 + C.i;
+        double G[3][3];
+        grad_cell(lo, hi, 0.25 / p.h, G);
+        lo = hi;
+        double s6[6];
+#pragma unroll
+        for (int a = 0; a < 6; a++) s6[a] = sig[a * nc + q];
+        predict_cell(p, c, G, s6, chi[q], q, nc, sig_star, dpl, sbar_out);
     }
 }
 
@@ -255,7 +280,8 @@ __global__ void k_div_rhs(StepParams p, const double *__restrict__ ss, double *_
     }
 }
 
-// Eq. (29): sigma = sigma* + dt (lam tr(D) I + 2 mu D), D = sym grad v
+// Eq. (29) over a column chunk of cells; chi_dst <- chi_src on the way
+// (the step's new chi, when chi_dst is not null)
 __global__ void k_stress_correct(StepParams p, const double *__restrict__ v,
                                  const double *__restrict__ ss, double *__restrict__ sig,
                                  const double *__restrict__ chi_src, double *__restrict__ chi_dst,
@@ -264,20 +290,50 @@ __global__ void k_stress_correct(StepParams p, const double *__restrict__ v,
     if (!cell_column(p.nx, p.ny, p.nz, C)) return;
     GradPlane lo = grad_plane(v, C.cs, C.k0 * C.pl, C.r0, C.r1, C.i, C.i1);
     for (int k = C.k0; k < C.k1; k++) {
-    const GradPlane hi = grad_plane(v, C.cs, (k + 1) * C.pl, C.r0, C.r1, C.i, C.i1);
-    const long q = k * C.pl + C.r0 + C.i;
-    double G[3][3];
-    grad_cell(lo, hi, 0.25 / p.h, G);
-    lo = hi;
-    const double tr = G[0][0] + G[1][1] + G[2][2];
-    const double dt = p.dt, lam = p.lam, mu = p.mu;
-    sig[0 * nc + q] = ss[0 * nc + q] + dt * (lam * tr + 2.0 * mu * G[0][0]);
-    sig[1 * nc + q] = ss[1 * nc + q] + dt * (lam * tr + 2.0 * mu * G[1][1]);
-    sig[2 * nc + q] = ss[2 * nc + q] + dt * (lam * tr + 2.0 * mu * G[2][2]);
-    sig[3 * nc + q] = ss[3 * nc + q] + dt * mu * (G[1][2] + G[2][1]);
-    sig[4 * nc + q] = ss[4 * nc + q] + dt * mu * (G[0][2] + G[2][0]);
-    sig[5 * nc + q] = ss[5 * nc + q] + dt * mu * (G[0][1] + G[1][0]);
-    if (chi_dst) chi_dst[q] = chi_src[q];
+        const GradPlane hi = grad_plane(v, C.cs, (k + 1) * C.pl, C.r0, C.r1, C.i, C.i1);
+        const long q = k * C.pl + C.r0 + C.i;
+        double G[3][3];
+        grad_cell(lo, hi, 0.25 / p.h, G);
+        lo = hi;
+        double s6[6], ss6[6];
+#pragma unroll
+        for (int a = 0; a < 6; a++) ss6[a] = ss[a * nc + q];
+        correct_cell(p, G, ss6, s6);
+#pragma unroll
+        for (int a = 0; a < 6; a++) sig[a * nc + q] = s6[a];
+        if (chi_dst) chi_dst[q] = chi_src[q];
+    }
+}
+
+// Eq. (29) of step n and Eq. (27) of step n+1 in one pass: both use the
+// gradient of the same velocity v^{n+1}, so it is formed once, and sigma^{n+1}
+// goes from the correction straight into the predictor without a round trip
+// through memory.  sig_star holds sigma* of step n on entry and of step n+1
+// on return (each cell reads and writes only its own entries); sig receives
+// sigma^{n+1}, chi_dst the step's new chi (chi_src).
+__global__ void k_correct_predict(StepParams p, StzConst c, const double *__restrict__ v,
+                                  double *__restrict__ sig_star, double *__restrict__ sig,
+                                  const double *__restrict__ chi_src,
+                                  double *__restrict__ chi_dst, double *__restrict__ dpl,
+                                  double *__restrict__ sbar_out, long nc) {
+    CellColumn C;
+    if (!cell_column(p.nx, p.ny, p.nz, C)) return;
+    GradPlane lo = grad_plane(v, C.cs, C.k0 * C.pl, C.r0, C.r1, C.i, C.i1);
+    for (int k = C.k0; k < C.k1; k++) {
+        const GradPlane hi = grad_plane(v, C.cs, (k + 1) * C.pl, C.r0, C.r1, C.i, C.i1);
+        const long q = k * C.pl + C.r0 + C.i;
+        double G[3][3];
+        grad_cell(lo, hi, 0.25 / p.h, G);
+        lo = hi;
+        double s6[6], ss6[6];
+#pragma unroll
+        for (int a = 0; a < 6; a++) ss6[a] = sig_star[a * nc + q];
+        correct_cell(p, G, ss6, s6);
+#pragma unroll
+        for (int a = 0; a < 6; a++) sig[a * nc + q] = s6[a];
+        const double chi_q = chi_src[q];
+        chi_dst[q] = chi_q;
+        predict_cell(p, c, G, s6, chi_q, q, nc, sig_star, dpl, sbar_out);
     }
 }
 
@@ -308,6 +364,178 @@ __global__ void k_wall_fill(WallParams w, double *__restrict__ v) {
     for (int a = 0; a < 3; a++) {
         v[a * cs + t] = bot[a];
         v[a * cs + (long)w.nz * pl + t] = top[a];
+    }
+}
+
+// ------------------------------------------------------------ explicit method
+// (section 3.2): forward Euler of Eqs. (24)-(26) with ENO advection (Eq. 33)
+
+// ENO first derivative, Eq. (33), from the values at offsets -2..2 along one
+// axis and the velocity component u along it: the one-sided three-point
+// stencil on the upwind side where that side is smoother than the centre,
+// else the centred difference.  The smoothness test compares the magnitudes
+// of the undivided second differences: the curvatures of Eq. (33) are those
+// divided by the same h^2 > 0, which cannot reorder them (the division is
+// monotone), and FP64 division is costly here; inv2h = 1 / (2h).
+__device__ __forceinline__ double eno_d(double fm2, double fm1, double f0, double fp1, double fp2,
+                                        double u, double inv2h) {
+    const double cm = fabs(f0 - 2.0 * fm1 + fm2);
+    const double c0 = fabs(fp1 - 2.0 * f0 + fm1);
+    const double cp = fabs(fp2 - 2.0 * fp1 + f0);
+    if (u < 0.0 && c0 > cp) return (-fp2 + 4.0 * fp1 - 3.0 * f0) * inv2h;
+    if (u > 0.0 && c0 > cm) return (3.0 * f0 - 4.0 * fm1 + fm2) * inv2h;
+    return (fp1 - fm1) * inv2h;
+}
+
+// Eq. (25) at cell centres: sigma' = sigma + dt (-(u.grad) sigma + L sigma +
+// sigma L^T - tr(L) sigma + C:(D - D^pl sigma0 / sbar)), L the Eq. (31)
+// gradient of v, u the mean of the cell's 8 corner velocities; the ENO
+// stencils reach two cells out, z ghost cells extrapolate each component
+// linearly from the two layers next to the wall; D^pl and sbar of the state
+// are written for the chi update
+__global__ void k_explicit_stress(StepParams p, StzConst c, const double *__restrict__ v,
+                                  const double *__restrict__ sig, const double *__restrict__ chi,
+                                  double *__restrict__ sig_new, double *__restrict__ dpl,
+                                  double *__restrict__ sbar_out, long nc) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    int i, j, k;
+    if (!cell_ijk(nx, ny, i, j, k)) return;
+    const long pl = (long)nx * ny, cs = (long)(nz + 1) * pl;
+    const int i1 = i + 1 < nx ? i + 1 : 0, j1 = j + 1 < ny ? j + 1 : 0;
+    const double h = p.h, inv2h = 0.5 / p.h;
+    double G[3][3], u[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double *g = v + a * cs;
+        const long b0 = (long)k * pl, b1 = b0 + pl, r0 = (long)j * nx, r1 = (long)j1 * nx;
+        const double c000 = g[b0 + r0 + i], c001 = g[b0 + r0 + i1], c010 = g[b0 + r1 + i],
+                     c011 = g[b0 + r1 + i1], c100 = g[b1 + r0 + i], c101 = g[b1 + r0 + i1],
+                     c110 = g[b1 + r1 + i], c111 = g[b1 + r1 + i1];
+        G[a][0] = ((c001 - c000) + (c011 - c010) + (c101 - c100) + (c111 - c110)) * (0.25 / h);
+        G[a][1] = ((c010 - c000) + (c011 - c001) + (c110 - c100) + (c111 - c101)) * (0.25 / h);
+        G[a][2] = ((c100 - c000) + (c110 - c010) + (c101 - c001) + (c111 - c011)) * (0.25 / h);
+        u[a] = 0.125 * (((c000 + c001) + (c010 + c011)) + ((c100 + c101) + (c110 + c111)));
+    }
+    const long q = (long)k * pl + (long)j * nx + i;
+    int ix[5], jy[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+        int a = i + m - 2, b = j + m - 2;
+        ix[m] = a < 0 ? a + nx : (a >= nx ? a - nx : a);
+        jy[m] = b < 0 ? b + ny : (b >= ny ? b - ny : b);
+    }
+    double s6[6], adv[6];
+#pragma unroll
+    for (int n = 0; n < 6; n++) {
+        const double *f = sig + n * nc;
+        s6[n] = f[q];
+        double fx[5], fy[5], fz[5];
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            fx[m] = f[(long)k * pl + (long)j * nx + ix[m]];
+            fy[m] = f[(long)k * pl + (long)jy[m] * nx + i];
+            const int kk = k + m - 2;
+            const long col = (long)j * nx + i;
+            if (kk < 0)
+                fz[m] = f[col] + kk * (f[pl + col] - f[col]);
+            else if (kk > nz - 1)
+                fz[m] = f[(long)(nz - 1) * pl + col] +
+                        (kk - (nz - 1)) * (f[(long)(nz - 1) * pl + col] - f[(long)(nz - 2) * pl + col]);
+            else
+                fz[m] = f[(long)kk * pl + col];
+        }
+        adv[n] = u[0] * eno_d(fx[0], fx[1], fx[2], fx[3], fx[4], u[0], inv2h) +
+                 u[1] * eno_d(fy[0], fy[1], fy[2], fy[3], fy[4], u[1], inv2h) +
+                 u[2] * eno_d(fz[0], fz[1], fz[2], fz[3], fz[4], u[2], inv2h);
+    }
+    const double S[3][3] = {{s6[0], s6[5], s6[4]}, {s6[5], s6[1], s6[3]}, {s6[4], s6[3], s6[2]}};
+    const double sb = sbar_of(s6);
+    const double inv_sb = sb > 0.0 ? 1.0 / sb : 0.0;
+    const double D = stz_rate(c, sb, inv_sb, chi[q]);
+    const double trL = G[0][0] + G[1][1] + G[2][2];
+    const double m3 = (s6[0] + s6[1] + s6[2]) * (1.0 / 3.0);
+    const double pl_ = (D > 0.0) ? 2.0 * p.mu * D * inv_sb : 0.0;
+    const int ia[6] = {0, 1, 2, 1, 0, 0}, ib[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+    for (int n = 0; n < 6; n++) {
+        const int a = ia[n], b = ib[n];
+        double rate = -adv[n] - trL * S[a][b];
+#pragma unroll
+        for (int e = 0; e < 3; e++) rate += G[a][e] * S[e][b] + S[a][e] * G[b][e];
+        rate += (a == b ? p.lam * trL : 0.0) + p.mu * (G[a][b] + G[b][a]);
+        rate -= pl_ * (S[a][b] - (a == b ? m3 : 0.0));
+        sig_new[n * nc + q] = S[a][b] + p.dt * rate;
+    }
+    dpl[q] = D;
+    sbar_out[q] = sb;
+}
+
+// Eq. (24) at interior corners (k = 1 .. nz-1):
+//   v' = v + dt (-(v.grad) v + div sigma / rho + kappa lap v),
+// the divergence the corner version of Eq. (31) over the 8 cells around the
+// corner, the Laplacian Eq. (32) along each axis, ENO advection with the
+// corner's own velocity; corners up to two planes beyond a wall reflect v
+// through the wall value, v(-m) = 2 v(0) - v(m)
+__global__ void k_explicit_velocity(StepParams p, double inv_rho, double kappa,
+                                    const double *__restrict__ v, const double *__restrict__ sig,
+                                    double *__restrict__ v_new, long nc) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z + 1;
+    if (i >= nx || j >= ny) return;
+    const long pl = (long)nx * ny, cs = (long)(nz + 1) * pl;
+    const double h = p.h, inv_h2 = 1.0 / (p.h * p.h), inv2h = 0.5 / p.h;
+    const int im = i ? i - 1 : nx - 1, jm = j ? j - 1 : ny - 1;
+    const int ip = i + 1 < nx ? i + 1 : 0, jp = j + 1 < ny ? j + 1 : 0;
+    const long node = (long)k * pl + (long)j * nx + i;
+    int ix[5], jy[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+        int a = i + m - 2, b = j + m - 2;
+        ix[m] = a < 0 ? a + nx : (a >= nx ? a - nx : a);
+        jy[m] = b < 0 ? b + ny : (b >= ny ? b - ny : b);
+    }
+    const double u[3] = {v[node], v[cs + node], v[2 * cs + node]};
+    const int comp[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    const long c0 = (long)(k - 1) * pl, c1 = (long)k * pl;
+    const long rm = (long)jm * nx, r0 = (long)j * nx;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double *fx = sig + comp[a][0] * nc, *fy = sig + comp[a][1] * nc,
+                     *fz = sig + comp[a][2] * nc;
+        const double div =
+            (((fx[c0 + rm + i] - fx[c0 + rm + im]) + (fx[c0 + r0 + i] - fx[c0 + r0 + im])) +
+             ((fx[c1 + rm + i] - fx[c1 + rm + im]) + (fx[c1 + r0 + i] - fx[c1 + r0 + im])) +
+             ((fy[c0 + r0 + im] - fy[c0 + rm + im]) + (fy[c0 + r0 + i] - fy[c0 + rm + i])) +
+             ((fy[c1 + r0 + im] - fy[c1 + rm + im]) + (fy[c1 + r0 + i] - fy[c1 + rm + i])) +
+             ((fz[c1 + rm + im] - fz[c0 + rm + im]) + (fz[c1 + rm + i] - fz[c0 + rm + i])) +
+             ((fz[c1 + r0 + im] - fz[c0 + r0 + im]) + (fz[c1 + r0 + i] - fz[c0 + r0 + i]))) *
+            (0.25 / h);
+        const double *g = v + a * cs;
+        const double w0 = g[node];
+        const double lap = ((g[node - i + ip] - 2.0 * w0 + g[node - i + im]) +
+                            (g[node - (long)j * nx + (long)jp * nx] - 2.0 * w0 +
+                             g[node - (long)j * nx + (long)jm * nx]) +
+                            (g[node + pl] - 2.0 * w0 + g[node - pl])) *
+                           inv_h2;
+        double fxl[5], fyl[5], fzl[5];
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            fxl[m] = g[(long)k * pl + (long)j * nx + ix[m]];
+            fyl[m] = g[(long)k * pl + (long)jy[m] * nx + i];
+            const int kk = k + m - 2;
+            const long col = (long)j * nx + i;
+            if (kk < 0)
+                fzl[m] = 2.0 * g[col] - g[(long)(-kk) * pl + col];
+            else if (kk > nz)
+                fzl[m] = 2.0 * g[(long)nz * pl + col] - g[(long)(2 * nz - kk) * pl + col];
+            else
+                fzl[m] = g[(long)kk * pl + col];
+        }
+        const double adv = u[0] * eno_d(fxl[0], fxl[1], fxl[2], fxl[3], fxl[4], u[0], inv2h) +
+                           u[1] * eno_d(fyl[0], fyl[1], fyl[2], fyl[3], fyl[4], u[1], inv2h) +
+                           u[2] * eno_d(fzl[0], fzl[1], fzl[2], fzl[3], fzl[4], u[2], inv2h);
+        v_new[a * cs + node] = w0 + p.dt * (-adv + div * inv_rho + kappa * lap);
     }
 }
 
@@ -358,8 +586,38 @@ cudaError_t stress_correct(const StepParams &p, const double *v, const double *s
     return cudaGetLastError();
 }
 
+cudaError_t correct_predict(const StepParams &p, const double *v, double *sig_star, double *sig,
+                            const double *chi_src, double *chi_dst, double *dpl, double *sbar,
+                            cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    k_correct_predict<<<cell_grid(p.nx, p.ny, (p.nz + kCellChunk - 1) / kCellChunk), kBlock, 0,
+                        s>>>(p, stz_const(p), v, sig_star, sig, chi_src, chi_dst, dpl, sbar, nc);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t wall_fill(const WallParams &w, double *v, cudaStream_t s) {
     k_wall_fill<<<cell_grid(w.nx, w.ny, 1), kBlock, 0, s>>>(w, v);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t explicit_stress(const StepParams &p, const double *v, const double *sig,
+                            const double *chi, double *sig_new, double *dpl, double *sbar,
+                            cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    k_explicit_stress<<<cell_grid(p.nx, p.ny, p.nz), kBlock, 0, s>>>(p, stz_const(p), v, sig, chi,
+                                                                     sig_new, dpl, sbar, nc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t explicit_velocity(const StepParams &p, double rho, double kappa, const double *v,
+                              const double *sig, double *v_new, cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    if (p.nz < 2) return cudaSuccess;
+    k_explicit_velocity<<<cell_grid(p.nx, p.ny, p.nz - 1), kBlock, 0, s>>>(p, 1.0 / rho, kappa, v,
+                                                                          sig, v_new, nc);
     count_launch();
     return cudaGetLastError();
 }

@@ -74,7 +74,22 @@ def test_reverse_mode_entry_points_reject_null_arguments_without_gpu():
     W = ctypes.c_double()
     assert L.qs_plastic_work_grad(None, None, 4, 1.0, 1e-10, 2, None, ctypes.byref(W),
                                   None) == binding.MG_ERR_ARG
+    assert L.qs_plastic_work(None, None, 4, 1.0, 1e-10, 2, None, ctypes.byref(W),
+                             None) == binding.MG_ERR_ARG
+    assert L.qs_plastic_work_backward(None, None, 0.0, 0, 4, 1.0, 1e-10, 2, None,
+                                      None) == binding.MG_ERR_ARG
     assert b"null" in L.mg_last_error()
+
+
+def test_qs_run_rejects_null_arguments_without_gpu():
+    L = binding.lib()
+    assert L.qs_run(None, None, 2, 1.0, 1e-10, None) == binding.MG_ERR_ARG
+    assert L.qs_step(None, None, 1.0, 1e-10, None) == binding.MG_ERR_ARG
+
+
+def test_explicit_step_rejects_null_arguments_without_gpu():
+    L = binding.lib()
+    assert L.qs_explicit_step(None, None, 1e-9, 6125.0, 1.0, 1) == binding.MG_ERR_ARG
 
 
 def test_plastic_work_is_an_autograd_function_over_the_c_entry_point():

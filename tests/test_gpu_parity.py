@@ -511,6 +511,63 @@ def test_qs_step_disc_walls_trajectory(kind):
     assert (np.abs(v[:, 0]).max() > 0) == (kind != 1)  # the bottom one with kinds 2, 3
 
 
+@pytest.mark.parametrize("n,nz,steps", [(16, None, 4), (24, 8, 3), (32, None, 3)])
+def test_qs_run_fused_steps(n, nz, steps):
+    """qs_run: each step's stress correction and the next step's predictor run
+    as one kernel.  FP64 with a fixed cycle count per step on both sides
+    (tol = 0), against the oracle's steps and against separate qs_step calls."""
+    w, v, sig, chi, t = _stz_state(n, nz, preload=1.2e9)
+    shape = (w.nx, w.ny, w.nz)
+    mg = O.MG(*shape, LAM, MU)
+    p = O.STZ(**w.stz)
+    bc = O.BC(**w.bc_values())
+    cyc = 10
+    v1, s1, c1 = g(v), g(sig), g(chi)
+    v2, s2, c2 = g(v), g(sig), g(chi)
+    run_state = make_state(v1, s1, c1, t)
+    step_state = make_state(v2, s2, c2, t)
+    for k in range(steps):
+        st, n_o, _ = O.qs_step(mg, v, sig, chi, w.h, w.dt, LAM, MU, p, bc, t, tol=0.0,
+                               max_cycles=cyc)
+        assert st == 0 and n_o == cyc
+        t += w.dt
+    ctx = ctx_for(shape, w=w, max_cycles=cyc)
+    st, stats = ctx.run(run_state, steps, w.dt, tol=0.0)
+    assert st == 0 and [s_.cycles for s_ in stats] == [cyc] * steps
+    assert run_state.step == steps and abs(run_state.t - t) <= 1e-15 * t
+    assert rel(c(v1), v) <= TOL64
+    assert rel(c(s1), sig) <= TOL64
+    assert rel(c(c1), chi) <= TOL64
+    for _ in range(steps):
+        ctx.step(step_state, w.dt, tol=0.0)
+    # same arithmetic in the same order: equal up to contraction choices
+    for a_, b_ in ((v1, v2), (s1, s2), (c1, c2)):
+        assert rel(c(a_), c(b_)) <= 1e-14
+    ctx.close()
+
+
+def test_qs_run_edge_cases():
+    """nsteps = 0 leaves the state alone; a solve that cannot converge stops
+    the run after its (completed) step."""
+    from paper_1904_03808_gb300 import binding
+    w, v, sig, chi, t = _stz_state(16, preload=1.2e9)
+    shape = (w.nx, w.ny, w.nz)
+    vg, sg, cg = g(v), g(sig), g(chi)
+    state = make_state(vg, sg, cg, t)
+    ctx = ctx_for(shape, w=w, max_cycles=1)
+    st, stats = ctx.run(state, 0, w.dt)
+    assert st == 0 and stats == [] and state.step == 0 and state.t == t
+    assert np.array_equal(c(vg), v) and np.array_equal(c(sg), sig) and np.array_equal(c(cg), chi)
+    st, stats = ctx.run(state, 3, w.dt, tol=1e-14, raise_on_error=False)
+    assert st == binding.MG_ERR_NOCONV
+    assert state.step == 1 and abs(state.t - (t + w.dt)) <= 1e-15 * t
+    assert stats[0].cycles == 1 and stats[0].rel_resid > 1e-14
+    # the stopped step is complete: its stress is the correction of its velocity
+    assert np.isfinite(c(sg)).all() and not np.array_equal(c(sg), sig)
+    assert ctx.run(state, -1, w.dt, raise_on_error=False)[0] == binding.MG_ERR_ARG
+    ctx.close()
+
+
 def test_qs_step_mixed_tracks_fp64():
     w, v, sig, chi, t = _stz_state(32, preload=1.2e9)
     shape = (w.nx, w.ny, w.nz)
