@@ -57,7 +57,9 @@ enum { MG_FP64 = 0, MG_MIXED = 1 };
 enum {
     MG_FLAG_COLOUR_PASSES = 1, /* FP32 sweeps: one launch per colour */
     MG_FLAG_NO_GRAPH = 2,      /* FP32 inner cycles: plain launches, no CUDA graph */
-    MG_FLAG_FUSED_SWEEP = 4    /* finest FP32 sweeps: both k-parities in one launch */
+    MG_FLAG_FUSED_SWEEP = 4,   /* finest FP32 sweeps: both k-parities in one launch */
+    MG_FLAG_UNFUSED_TRANSFERS = 8 /* finest FP32 residual and restriction as
+                                     separate passes */
 };
 enum { MG_HIST = 128 };
 
@@ -109,7 +111,10 @@ typedef struct {
  *                 k-parities, with ready flags between neighbouring row
  *                 strips) instead of two, where the grid suits it: a third
  *                 less DRAM traffic, but slower on GB300 (same arithmetic;
- *                 kept for comparison).
+ *                 kept for comparison); MG_FLAG_UNFUSED_TRANSFERS runs the
+ *                 finest-level FP32 residual and its restriction as two passes
+ *                 with the residual stored instead of one fused pass (kept
+ *                 for comparison).
  */
 typedef struct {
     int precision;
@@ -234,6 +239,18 @@ mg_status mg_residual(mg_ctx *ctx, int level, const double *b, const double *x, 
  * pass through the solver's own FP32 buffers, so this call must not overlap
  * an mg_solve / qs_step on the same context. */
 mg_status mg_residual32(mg_ctx *ctx, int level, const float *b, const float *x, float *r);
+
+/* bc = T^T (b - A_level x) in FP32 (level -> level + 1): the residual and its
+ * restriction (section 3.6), as the mixed-precision V-cycle computes them.
+ * On the finest level, where its row-strip kernel takes the grid, the two
+ * are fused and the residual is never stored: the kernel applies the x and y
+ * parts of the full weighting to each tile's residual and a second kernel
+ * the z part.  b, x: (3, nz+1, ny, nx) of the level, natural column order;
+ * bc: the next level's (3, nz/2+1, ny/2, nx/2), wall planes not written.
+ * Uses the solver's own FP32 buffers (must not overlap a solve on the same
+ * context).  Errors: MG_ERR_ARG (null array, no coarser level), MG_ERR_CUDA. */
+mg_status mg_residual_restrict32(mg_ctx *ctx, int level, const float *b, const float *x,
+                                 float *bc);
 
 /* nsweeps Gauss-Seidel sweeps on level `level`, colours 0..7 if
  * descending == 0 else 7..0; FP64 (precision 0) or FP32 arrays (precision 1). */

@@ -22,6 +22,7 @@ MG_FP64, MG_MIXED = 0, 1
 MG_FLAG_COLOUR_PASSES = 1
 MG_FLAG_NO_GRAPH = 2
 MG_FLAG_FUSED_SWEEP = 4
+MG_FLAG_UNFUSED_TRANSFERS = 8
 MG_HIST = 128
 
 
@@ -82,6 +83,7 @@ _SIGS = {
     "mg_level_stencil": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
     "mg_residual": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_residual32": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "mg_residual_restrict32": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_smooth": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_int, C.c_int]),
     "mg_restrict": (C.c_int, [_P, C.c_int, _P, _P]),
     "mg_prolong_add": (C.c_int, [_P, C.c_int, _P, _P]),
@@ -323,6 +325,13 @@ class Context:
         import torch
         _check(lib().mg_residual32(self.h, level, _ptr(b, torch.float32), _ptr(x, torch.float32),
                                    _ptr(r, torch.float32)), "mg_residual32")
+
+    def residual_restrict32(self, level, b, x, bc):
+        """mg_residual_restrict32: bc = T^T (b - A x) in FP32 (float32 tensors)."""
+        import torch
+        _check(lib().mg_residual_restrict32(self.h, level, _ptr(b, torch.float32),
+                                            _ptr(x, torch.float32), _ptr(bc, torch.float32)),
+               "mg_residual_restrict32")
 
     def smooth(self, level, b, x, nsweeps, descending=False):
         import torch

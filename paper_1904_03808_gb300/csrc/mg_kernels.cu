@@ -292,6 +292,23 @@ __global__ void k_restrict(Dims f, Dims c, const T *__restrict__ r, T *__restric
     bc[p + 2 * c.cs] = s2;
 }
 
+// z part of the full weighting, after the fused fine residual of
+// smoother_rows.cu has applied the x and y parts: bc(I, J, K) = 1/2 p(2K-1)
+// + p(2K) + 1/2 p(2K+1), p(k) the partial sums of fine plane k, laid out
+// [c][k][J][I] with component stride pcs; coarse interior nodes
+__global__ void k_restrict_z(Dims c, long pcs, const float *__restrict__ p,
+                             float *__restrict__ bc) {
+    int I, J, K;
+    if (!node_ijk(c, I, J, K)) return;
+    const long pl = (long)c.ny * c.nx, q = (long)J * c.nx + I;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float *pa = p + a * pcs + q;
+        bc[a * c.cs + K * pl + q] =
+            (0.5f * pa[(2 * K - 1) * pl] + pa[2 * K * pl]) + 0.5f * pa[(2 * K + 1) * pl];
+    }
+}
+
 // prolongation x += T xc: fine node 2I is coarse node I, odd fine nodes take
 // the mean of their two neighbours along each odd axis (coarse walls are 0).
 // One thread per coarse cell (I, J, K): it loads the cell's 8 corners once
@@ -550,6 +567,15 @@ cudaError_t restrict_fw(const Dims &fine, const double *r, double *bc, cudaStrea
 }
 cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_t s, int split) {
     return restrict_t(fine, r, bc, s, split);
+}
+
+cudaError_t restrict_z(const Dims &fine, const float *part, float *bc, cudaStream_t s) {
+    const Dims c = make_dims(fine.nx / 2, fine.ny / 2, fine.nz / 2);
+    if (c.nz < 2) return cudaSuccess;
+    const long pcs = (long)(fine.nz + 1) * c.ny * c.nx;
+    k_restrict_z<<<node_grid(c.nx, c.ny, c.nz - 1), kBlock, 0, s>>>(c, pcs, part, bc);
+    count_launch();
+    return cudaGetLastError();
 }
 
 template <typename T>

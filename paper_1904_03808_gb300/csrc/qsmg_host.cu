@@ -555,6 +555,31 @@ inline cudaError_t prolong_add_any(const Dims &d, const float *xc, float *x, cud
     return prolong_add(d, xc, x, s, split);
 }
 
+// bc = T^T (b - A_l x) on level l; r is level l's residual buffer
+template <typename T>
+mg_status residual_restrict_level(mg_ctx *ctx, int l, const T *b, const T *x, T *r, T *bc) {
+    CKS(residual_level<T>(ctx, l, b, x, r));
+    CK(restrict_fw_any(ctx->L[l], r, bc, ctx->st, split_of<T>(ctx, l)));
+    return MG_OK;
+}
+
+// FP32 finest level: residual and restriction fused where the row-strip
+// kernel takes the grid (the residual is never stored; r receives the
+// per-plane partial sums), else the two passes
+template <>
+mg_status residual_restrict_level<float>(mg_ctx *ctx, int l, const float *b, const float *x,
+                                         float *r, float *bc) {
+    if (l == 0 && !(ctx->opts.flags & MG_FLAG_UNFUSED_TRANSFERS)) {
+        const cudaError_t e =
+            residual_restrict_fine_rows(ctx->L[0], ctx->f32, b, x, r, bc, ctx->st, ctx->split0);
+        if (e == cudaSuccess) return MG_OK;
+        if (e != cudaErrorNotSupported) CK(e);
+    }
+    CKS(residual_level<float>(ctx, l, b, x, r));
+    CK(restrict_fw_any(ctx->L[l], r, bc, ctx->st, split_of<float>(ctx, l)));
+    return MG_OK;
+}
+
 // one V-cycle for A_l x = b on level l (section 3.6)
 template <typename T>
 mg_status vcycle(mg_ctx *ctx, int l, const T *b, T *x) {
@@ -565,9 +590,8 @@ mg_status vcycle(mg_ctx *ctx, int l, const T *b, T *x) {
         return MG_OK;
     }
     CKS(smooth<T>(ctx, l, b, x, ctx->opts.nu1, false));
-    CKS(residual_level<T>(ctx, l, b, x, r));
     T *bc = Bufs<T>::b(ctx, l + 1), *xc = Bufs<T>::x(ctx, l + 1);
-    CK(restrict_fw_any(ctx->L[l], r, bc, ctx->st, split_of<T>(ctx, l)));
+    CKS(residual_restrict_level<T>(ctx, l, b, x, r, bc));
     CK(cudaMemsetAsync(xc, 0, corner_count(ctx->L[l + 1]) * sizeof(T), ctx->st));
     CKS(vcycle<T>(ctx, l + 1, bc, xc));
     CK(prolong_add_any(ctx->L[l], xc, x, ctx->st, split_of<T>(ctx, l)));
@@ -1159,26 +1183,47 @@ mg_status mg_residual32(mg_ctx *ctx, int level, const float *b, const float *x, 
     return MG_OK;
 }
 
-mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps, int descending,
-                    int precision) {
-    CKS(level_arg(ctx, level, 0));
-    if (!b || !x || nsweeps < 0) {
-        set_err("mg_smooth: bad arguments");
+mg_status mg_residual_restrict32(mg_ctx *ctx, int level, const float *b, const float *x,
+                                 float *bc) {
+    CKS(level_arg(ctx, level, 1));
+    if (!b || !x || !bc) {
+        set_err("mg_residual_restrict32: null array");
         return MG_ERR_ARG;
     }
-    if (precision == MG_FP64) {
-        CKS(smooth<double>(ctx, level, (const double *)b, (double *)x, nsweeps, descending != 0));
-    } else if (level == 0 && ctx->split0) {
+    float *r = ctx->r32[level];
+    if (level == 0 && ctx->split0) {
+        // natural-order caller arrays through the solver's parity-split buffers
+        const Dims &d = ctx->L[0];
+        const size_t plane = (size_t)d.ny * d.nx;
+        CK(split_columns(d, x, ctx->x32[0], true, ctx->st));
+        CK(split_columns(d, b, ctx->b32[0], true, ctx->st));
+        CKS(residual_restrict_level<float>(ctx, 0, ctx->b32[0], ctx->x32[0], r, bc));
+        for (int c = 0; c < 3; c++) {  // the solver relies on zero walls in x32[0]
+            CK(cudaMemsetAsync(ctx->x32[0] + c * d.cs, 0, plane * sizeof(float), ctx->st));
+            CK(cudaMemsetAsync(ctx->x32[0] + c * d.cs + d.nz * plane, 0, plane * sizeof(float),
+                               ctx->st));
+        }
+    } else {
+        CKS(residual_restrict_level<float>(ctx, level, b, x, r, bc));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+// FP32 sweeps of a component entry point
+static mg_status smooth32_entry(mg_ctx *ctx, int level, const float *b, float *x, int nsweeps,
+                                bool descending) {
+    if (level == 0 && ctx->split0) {
         // the caller's arrays are in natural order: convert through the
         // solver's own finest FP32 buffers
         const Dims &d = ctx->L[0];
         const size_t plane = (size_t)d.ny * d.nx;
-        CK(split_columns(d, (const float *)x, ctx->x32[0], true, ctx->st));
-        CK(split_columns(d, (const float *)b, ctx->b32[0], true, ctx->st));
+        CK(split_columns(d, x, ctx->x32[0], true, ctx->st));
+        CK(split_columns(d, b, ctx->b32[0], true, ctx->st));
         CK(cudaMemcpyAsync(ctx->xs32[0], ctx->x32[0], 3 * (size_t)d.cs * sizeof(float),
                            cudaMemcpyDeviceToDevice, ctx->st));  // partner gets the walls
-        CKS(smooth<float>(ctx, 0, ctx->b32[0], ctx->x32[0], nsweeps, descending != 0));
-        CK(split_columns(d, ctx->x32[0], (float *)x, false, ctx->st));
+        CKS(smooth<float>(ctx, 0, ctx->b32[0], ctx->x32[0], nsweeps, descending));
+        CK(split_columns(d, ctx->x32[0], x, false, ctx->st));
         // the solver relies on zero walls in x32[0] and its partner
         for (float *w : {ctx->x32[0], ctx->xs32[0]})
             for (int c = 0; c < 3; c++) {
@@ -1187,12 +1232,26 @@ mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps,
                                    ctx->st));
             }
     } else {
-        CKS(smooth<float>(ctx, level, (const float *)b, (float *)x, nsweeps, descending != 0));
+        CKS(smooth<float>(ctx, level, b, x, nsweeps, descending));
     }
     if (ctx->has_sync)
         CK(cudaMemcpyAsync(ctx->herr, ctx->sync.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return sync_error(ctx);
+}
+
+mg_status mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nsweeps, int descending,
+                    int precision) {
+    CKS(level_arg(ctx, level, 0));
+    if (!b || !x || nsweeps < 0) {
+        set_err("mg_smooth: bad arguments");
+        return MG_ERR_ARG;
+    }
+    if (precision != MG_FP64)
+        return smooth32_entry(ctx, level, (const float *)b, (float *)x, nsweeps, descending != 0);
+    CKS(smooth<double>(ctx, level, (const double *)b, (double *)x, nsweeps, descending != 0));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
 }
 
 mg_status mg_restrict(mg_ctx *ctx, int level, const double *r, double *bc) {

@@ -189,6 +189,13 @@ cudaError_t sumsq(const Dims &d, const double *r, double *partials, cudaStream_t
 cudaError_t sum_partials(const double *partials, double *out, cudaStream_t s);
 
 cudaError_t restrict_fw(const Dims &fine, const double *r, double *bc, cudaStream_t s);
+// z part of the full weighting over the x-y partial sums [c][k][J][I] of
+// every fine plane (component stride (nz+1) ny/2 nx/2)
+cudaError_t restrict_z(const Dims &fine, const float *part, float *bc, cudaStream_t s);
+// fused finest FP32 residual + restriction (row strips), or cudaErrorNotSupported
+cudaError_t residual_restrict_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
+                                        const float *x, float *part, float *bc, cudaStream_t s,
+                                        int split);
 cudaError_t restrict_fw(const Dims &fine, const float *r, float *bc, cudaStream_t s,
                         int split = 0);
 cudaError_t prolong_add(const Dims &fine, const double *xc, double *x, cudaStream_t s);

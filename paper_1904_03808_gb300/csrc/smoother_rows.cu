@@ -304,7 +304,7 @@ cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, cons
 // Measured on GB300 and dropped: one CTA per SM with double-buffered stages
 // and four z-plane slots (24% slower); issuing the next tile's right-hand
 // side and z-plane copies right after the first pass, when they are dead
-// (6% slower); right-hand-side rows loaded from global memory into
+// (6% slower, measured twice); right-hand-side rows loaded from global memory into
 // registers instead of staged (freeing shared memory for taller tiles or a
 // third CTA per SM: 10-17% slower); a cyclic plane-major tile order (27%
 // fewer DRAM bytes, 18% slower: it loses the z-plane reuse); one thread per
@@ -501,7 +501,11 @@ __device__ __forceinline__ void pers_update(const OP &op, float (&P)[3][2][R],
 
 // One sweep phase (or, with RES, the residual b - A x of every plane
 // k = kbase, kbase + kstep, ...; then F = 0, vin = zsrc = x, vout = r).
-template <class OP, int F, bool SPLIT, bool RES>
+// With RES and RR (F = 1) the residual is not stored: each tile applies the
+// x and y parts of the restriction to it and vout receives, per fine plane,
+// the coarse-grid partial sums [c][k][J][I] (c stride (nz+1) ny/2 nx/2) that
+// k_restrict_z combines along z.
+template <class OP, int F, bool SPLIT, bool RES, bool RR = false>
 __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
     k_gs_rows_p(Dims d, OP op, const float *__restrict__ b, const float *__restrict__ vin,
                 const float *__restrict__ zsrc, float *__restrict__ vout, int kbase, int kstep,
@@ -612,9 +616,12 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
             }
         if (RES) {
             // residual of the tile rows 1 .. TY: numerator - centre block x
-            float res[3][2][TY + 1];
+            // (with RR rows 1 .. TY + 1, i.e. y0 - 1 .. y0 + TY - 1: the fine
+            // rows of the strip's coarse rows)
+            constexpr int NR = RR ? TY + 2 : TY + 1;
+            float res[3][2][NR];
 #pragma unroll
-            for (int jj = 1; jj < TY + 1; jj++) {
+            for (int jj = 1; jj < NR; jj++) {
                 float num[3], x[3], cx[3];
                 op.template numer<0, R>(P, r, Ps, q, jj, num);
 #pragma unroll
@@ -629,13 +636,46 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
 #pragma unroll
                 for (int c = 0; c < 3; c++) res[c][1][jj] = num[c] - cx[c];
             }
+            if (RR) {
+                // full weighting R = T^T (weight 1 at offset 0, 1/2 at +-1 per
+                // axis), x and y parts: coarse column I = t takes fine
+                // x = 2t - 1 (the O node of thread t - 1), 2t, 2t + 1; coarse
+                // row J = y0/2 + jc takes fine rows 2J - 1 .. 2J + 1, window
+                // rows 2 jc + 1 .. 2 jc + 3.  The O residuals go through the
+                // (now dead) plane rows in shared memory.
+                __syncthreads();
+                float *Xo = Ps;
 #pragma unroll
-            for (int c = 0; c < 3; c++)
+                for (int c = 0; c < 3; c++)
 #pragma unroll
-                for (int jj = 1; jj < TY + 1; jj++) {
-                    P[c][0][jj] = res[c][0][jj];
-                    P[c][1][jj] = res[c][1][jj];
+                    for (int jj = 1; jj < NR; jj++) Xo[(c * NR + jj) * hn + t] = res[c][1][jj];
+                __syncthreads();
+                const int hny = ny >> 1;
+                const long pcs = (long)(d.nz + 1) * hny * hn;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    float rx[NR];
+#pragma unroll
+                    for (int jj = 1; jj < NR; jj++)
+                        rx[jj] = (0.5f * Xo[(c * NR + jj) * hn + tm] + res[c][0][jj]) +
+                                 0.5f * res[c][1][jj];
+#pragma unroll
+                    for (int jc = 0; jc < TY / 2; jc++) {
+                        const int J = (y0 >> 1) + jc;
+                        if (J < hny)
+                            vout[c * pcs + ((long)k * hny + J) * hn + t] =
+                                (0.5f * rx[2 * jc + 1] + rx[2 * jc + 2]) + 0.5f * rx[2 * jc + 3];
+                    }
                 }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+#pragma unroll
+                    for (int jj = 1; jj < TY + 1; jj++) {
+                        P[c][0][jj] = res[c][0][jj];
+                        P[c][1][jj] = res[c][1][jj];
+                    }
+            }
         } else {
             constexpr int EF = F, EG = 1 - F;
             const int xF = EF == 0 ? q.xe : q.xo, xG = EG == 0 ? q.xe : q.xo;
@@ -672,7 +712,7 @@ __global__ void __launch_bounds__(kPersMaxNx / 2, kPersMinBlocks)
 #pragma unroll
         for (int jj = 1 + F; jj < TY + 1 + F; jj++) {
             const int y = y0 - 1 - F + jj;
-            if (y < ny) {
+            if (!RR && y < ny) {
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     Ok[c * cs + (long)y * nx + q.xe] = P[c][0][jj];
@@ -697,7 +737,7 @@ inline long pers_slots(int nx, int sms) {
     return (long)sms * kPersMinBlocks * (kPersMaxNx / nx);
 }
 
-template <class OP, int F, bool SPLIT, bool RES>
+template <class OP, int F, bool SPLIT, bool RES, bool RR = false>
 cudaError_t launch_rows_p(const Dims &d, const OP &op, const float *b, const float *vin,
                           const float *zsrc, float *vout, int kbase, int kstep, int nplanes,
                           cudaStream_t s, int sms) {
@@ -706,7 +746,7 @@ cudaError_t launch_rows_p(const Dims &d, const OP &op, const float *b, const flo
     const long ntiles = (long)nstrips * nplanes;
     const long slots = pers_slots(d.nx, sms);
     const int grid = (int)(ntiles < slots ? ntiles : slots);
-    k_gs_rows_p<OP, F, SPLIT, RES><<<grid, d.nx / 2, pers_floats(d.nx) * sizeof(float), s>>>(
+    k_gs_rows_p<OP, F, SPLIT, RES, RR><<<grid, d.nx / 2, pers_floats(d.nx) * sizeof(float), s>>>(
         d, op, b, vin, zsrc, vout, kbase, kstep, nplanes, nstrips);
     count_launch();
     return cudaGetLastError();
@@ -1118,6 +1158,8 @@ cudaError_t smoother_init() {
     SET((k_gs_rows_p<FineRowsOp, 1, true, false>), smem_p)
     SET((k_gs_rows_p<FineRowsOp, 0, false, true>), smem_p)
     SET((k_gs_rows_p<FineRowsOp, 0, true, true>), smem_p)
+    SET((k_gs_rows_p<FineRowsOp, 1, false, true, true>), smem_p)
+    SET((k_gs_rows_p<FineRowsOp, 1, true, true, true>), smem_p)
     SET((k_gs_rows_p<CoarseRowsOp, 0, false, false>), smem_p)
     SET((k_gs_rows_p<CoarseRowsOp, 1, false, false>), smem_p)
     const int smem_f = smem_p;
@@ -1203,6 +1245,28 @@ cudaError_t residual_fine_rows(const Dims &d, const Fine<float> &f, const float 
                                                             sms)
                  : launch_rows_p<FineRowsOp, 0, false, true>(d, op, b, x, x, r, 1, 1, d.nz - 1,
                                                              s, sms);
+}
+
+// The finest FP32 residual restricted to the next level without storing it
+// (rows as residual_fine_rows; ny even and nz >= 4 even): the residual
+// kernel writes the x-y restricted partial sums of every fine plane into
+// part (3 (nz+1) ny/2 nx/2 floats), k_restrict_z combines them along z into
+// bc; or cudaErrorNotSupported.
+cudaError_t residual_restrict_fine_rows(const Dims &d, const Fine<float> &f, const float *b,
+                                        const float *x, float *part, float *bc, cudaStream_t s,
+                                        int split) {
+    int sms = 0;
+    static_assert(kPersTY % 2 == 0, "coarse rows of a strip need an even strip height");
+    if ((d.ny & 1) || d.nz < 4 || (d.nz & 1) || !rows_p_ok(d, b, x, part, sms))
+        return cudaErrorNotSupported;
+    const FineRowsOp op{f};
+    const cudaError_t e =
+        split ? launch_rows_p<FineRowsOp, 1, true, true, true>(d, op, b, x, x, part, 1, 1,
+                                                                d.nz - 1, s, sms)
+              : launch_rows_p<FineRowsOp, 1, false, true, true>(d, op, b, x, x, part, 1, 1,
+                                                                 d.nz - 1, s, sms);
+    if (e != cudaSuccess) return e;
+    return restrict_z(d, part, bc, s);
 }
 
 // Coarse levels take the row strips only where they win (measured on GB300,

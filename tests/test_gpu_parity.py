@@ -98,6 +98,33 @@ def test_residual32_every_level(shape):
     ctx.close()
 
 
+@pytest.mark.parametrize("shape", [(256, 32, 32), (128, 40, 32), (192, 24, 16), (64, 64, 64),
+                                   (128, 64, 32), (72, 40, 16), (16, 8, 12)])
+def test_residual_restrict32(shape):
+    """The FP32 residual and its restriction as the V-cycle computes them:
+    fused without storing the residual on the finest level where the row-strip
+    kernel takes the grid (rows of 64/128/192/256 nodes; ny = 40 leaves a
+    ragged last strip of 4 rows), else residual then restriction; against the oracle's restriction of its residual on the same
+    FP32-rounded arrays, every level with a coarser one."""
+    rng = np.random.default_rng(17)
+    ctx = ctx_for(shape, precision=MG_MIXED)
+    mg = O.MG(*shape, LAM, MU)
+    for l in range(mg.levels - 1):
+        d, dc = mg.dims(l), mg.dims(l + 1)
+        x = rand_corner(rng, d).astype(np.float32).astype(np.float64)
+        b = rand_corner(rng, d).astype(np.float32).astype(np.float64)
+        if l > 0:
+            x[:, [0, d[2]]] = 0
+        bc = torch.zeros((3, dc[2] + 1, dc[1], dc[0]), dtype=torch.float32, device="cuda")
+        ctx.residual_restrict32(l, g(b, torch.float32), g(x, torch.float32), bc)
+        want = O.restrict(O.residual(mg.stencil(l), b, x))
+        got = c(bc).astype(np.float64)
+        assert np.isfinite(got).all()
+        assert not got[:, [0, dc[2]]].any()  # wall planes untouched (zero)
+        assert rel(got, want) <= 2e-6, (l, rel(got, want))
+    ctx.close()
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_residual_every_level(shape):
     rng = np.random.default_rng(1)
@@ -343,6 +370,35 @@ def test_mixed_solve_reaches_tolerance(shape, inner):
     assert np.sqrt(O.norm2(r) / O.norm2(bl)) <= 1.05e-10
     err = rel(vgn, vo)
     assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (256, 32, 32), (128, 48, 32)])
+@pytest.mark.parametrize("flags", [0, 8])
+def test_mixed_solve_fused_transfers(shape, flags):
+    """The mixed solve with the finest level's residual and restriction fused
+    into one row-strip pass (flags 0) and as separate passes (flags 8,
+    MG_FLAG_UNFUSED_TRANSFERS): both reach the tolerance, checked
+    with the oracle's operator, and stay within 1e-6 of the oracle's FP64
+    solution (256 x 32 x 32 has a ragged last row strip)."""
+    nx, ny, nz = shape
+    b = I.rhs_field(2, nx, ny, nz)
+    v = np.zeros_like(b)
+    v[0, 0], v[0, nz] = -1.0, 1.0
+    mg = O.MG(nx, ny, nz, LAM, MU)
+    vo = v.copy()
+    mg.solve(b, vo, 1e-12, 200)
+    ctx = ctx_for(shape, precision=MG_MIXED, max_cycles=60, flags=flags)
+    vg = g(v)
+    st, s = ctx.solve(g(b), vg, tol=1e-10)
+    assert st == 0 and s.rel_resid <= 1e-10
+    vgn = c(vg)
+    r = O.residual(mg.stencil(0), b, vgn)
+    w = np.zeros_like(v)
+    w[:, 0], w[:, nz] = v[:, 0], v[:, nz]
+    bl = O.residual(mg.stencil(0), b, w)
+    assert np.sqrt(O.norm2(r) / O.norm2(bl)) <= 1.05e-10
+    assert rel(vgn, vo) <= 1e-6
+    ctx.close()
 
 
 @pytest.mark.parametrize("inner", [0, 4])
