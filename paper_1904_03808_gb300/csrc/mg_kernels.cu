@@ -325,6 +325,7 @@ __global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restric
     const int ci[2] = {I, I1};
     const int fcol[2] = {colmap(2 * I, f.nx, split), colmap(2 * I + 1, f.nx, split)};
     const T h = T(0.5);
+    T w[3][2][2][2];  // [component][coarse z][fine b][fine a]
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         const T *X = xc + a * c.cs + (long)K * cps;
@@ -335,7 +336,6 @@ __global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restric
             for (int y = 0; y < 2; y++)
 #pragma unroll
                 for (int e = 0; e < 2; e++) v[z][y][e] = X[z * cps + cr[y] + ci[e]];
-        T w[2][2][2];  // [fine c][fine b][fine a]
 #pragma unroll
         for (int z = 0; z < 2; z++) {
             T ax[2][2];  // [y][fine a]
@@ -346,25 +346,43 @@ __global__ void k_prolong(Dims f, Dims c, const T *__restrict__ xc, T *__restric
             }
 #pragma unroll
             for (int e = 0; e < 2; e++) {
-                w[z][0][e] = ax[0][e];
-                w[z][1][e] = h * (ax[0][e] + ax[1][e]);
-            }
-        }
-#pragma unroll
-        for (int cz = 0; cz < 2; cz++) {
-            const int k = 2 * K + cz;
-            if (k == 0) continue;
-#pragma unroll
-            for (int bb = 0; bb < 2; bb++) {
-                T *row = x + a * f.cs + (long)k * fps + (long)(2 * J + bb) * f.nx;
-#pragma unroll
-                for (int e = 0; e < 2; e++) {
-                    const T val = cz ? h * (w[0][bb][e] + w[1][bb][e]) : w[0][bb][e];
-                    row[fcol[e]] += val;
-                }
+                w[a][z][0][e] = ax[0][e];
+                w[a][z][1][e] = h * (ax[0][e] + ax[1][e]);
             }
         }
     }
+    // every fine value of the block is loaded before any is stored: as far
+    // as the compiler knows a store may alias a later load, so interleaved
+    // read-modify-writes would wait for one DRAM round trip each
+    const int cz0 = K == 0 ? 1 : 0;  // fine plane 0 is a wall
+    T old[3][2][2][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int cz = 0; cz < 2; cz++) {
+            if (cz < cz0) continue;
+#pragma unroll
+            for (int bb = 0; bb < 2; bb++) {
+                const T *row = x + a * f.cs + (long)(2 * K + cz) * fps + (long)(2 * J + bb) * f.nx;
+#pragma unroll
+                for (int e = 0; e < 2; e++) old[a][cz][bb][e] = row[fcol[e]];
+            }
+        }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int cz = 0; cz < 2; cz++) {
+            if (cz < cz0) continue;
+#pragma unroll
+            for (int bb = 0; bb < 2; bb++) {
+                T *row = x + a * f.cs + (long)(2 * K + cz) * fps + (long)(2 * J + bb) * f.nx;
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const T val = cz ? h * (w[a][0][bb][e] + w[a][1][bb][e]) : w[a][0][bb][e];
+                    row[fcol[e]] = old[a][cz][bb][e] + val;
+                }
+            }
+        }
 }
 
 // x += Ainv r on the coarsest level; one warp per unknown, fixed-order sums.
@@ -405,8 +423,17 @@ __global__ void k_axpy_f32(Dims d, double scale, const float *__restrict__ e,
     if (!node_ijk(d, i, j, k)) return;
     const long row = ((long)k * d.ny + j) * d.nx;
     const long p = row + i, pe = row + colmap(i, d.nx, split);
+    // all loads before the stores (a store may alias a later load as far as
+    // the compiler knows, which would serialise the three round trips)
+    double vo[3];
+    float eo[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) v[a * d.cs + p] += scale * (double)e[a * d.cs + pe];
+    for (int a = 0; a < 3; a++) {
+        vo[a] = v[a * d.cs + p];
+        eo[a] = e[a * d.cs + pe];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) v[a * d.cs + p] = vo[a] + scale * (double)eo[a];
 }
 
 // natural <-> parity-split column order of a whole corner array
