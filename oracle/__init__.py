@@ -100,6 +100,8 @@ def lib():
         L.ora_qs_step.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                   C.POINTER(STZ), C.POINTER(BC), C.c_double, _D, _D, _D,
                                   C.c_double, C.c_int, _I, _D]
+        L.ora_stress_star_adv.argtypes = L.ora_stress_star.argtypes + [C.c_int]
+        L.ora_qs_step_adv.argtypes = L.ora_qs_step.argtypes + [C.c_int]
         L.ora_eno.argtypes = [_D, C.c_double, C.c_double]
         L.ora_eno.restype = C.c_double
         L.ora_explicit_step.argtypes = [C.c_int, C.c_int, C.c_int] + [C.c_double] * 6 + [
@@ -229,13 +231,14 @@ def cell_gradient(v, h) -> np.ndarray:
     return L
 
 
-def stress_star(v, sig, chi, h, dt, mu, stz):
+def stress_star(v, sig, chi, h, dt, mu, stz, advect=False):
+    """Eq. (27); advect adds -(u.grad) sigma (ENO, Eq. 33) to the rate."""
     nx, ny, nz = _dims(v)
     ss = np.zeros_like(sig)
     D = np.zeros_like(chi)
     sb = np.zeros_like(chi)
-    lib().ora_stress_star(nx, ny, nz, h, dt, mu, C.byref(stz), _p(v), _p(sig), _p(chi),
-                          _p(ss), _p(D), _p(sb))
+    lib().ora_stress_star_adv(nx, ny, nz, h, dt, mu, C.byref(stz), _p(v), _p(sig), _p(chi),
+                              _p(ss), _p(D), _p(sb), 1 if advect else 0)
     return ss, D, sb
 
 
@@ -264,12 +267,15 @@ def wall_fill(v, h, bc: BC, t: float) -> None:
     lib().ora_wall_fill(*_dims(v), h, C.byref(bc), t, _p(v))
 
 
-def qs_step(mg: MG, v, sig, chi, h, dt, lam, mu, stz: STZ, bc: BC, t, tol=1e-10, max_cycles=100):
-    """One projection step in place; returns (status, cycles, history)."""
+def qs_step(mg: MG, v, sig, chi, h, dt, lam, mu, stz: STZ, bc: BC, t, tol=1e-10, max_cycles=100,
+            advect=False):
+    """One projection step in place (advect: the stress advection of
+    stress_star); returns (status, cycles, history)."""
     cyc = C.c_int(0)
     hist = np.zeros(max_cycles + 1)
-    st = lib().ora_qs_step(mg.h, h, dt, lam, mu, C.byref(stz), C.byref(bc), t, _p(v), _p(sig),
-                           _p(chi), tol, max_cycles, C.byref(cyc), _p(hist))
+    st = lib().ora_qs_step_adv(mg.h, h, dt, lam, mu, C.byref(stz), C.byref(bc), t, _p(v),
+                               _p(sig), _p(chi), tol, max_cycles, C.byref(cyc), _p(hist),
+                               1 if advect else 0)
     return st, cyc.value, hist[: cyc.value + 1].copy()
 
 

@@ -39,7 +39,11 @@
  *     kappa a diffusivity (m^2/s; section 4 sets kappa = kappa' h and the
  *     stability limit dt <= h^2 / (6 kappa)); sigma is advected with the mean
  *     of its cell's corner velocities; ghost values two planes beyond a wall
- *     reflect v through the wall value and extrapolate cell fields linearly.
+ *     reflect v through the wall value and extrapolate cell fields linearly;
+ *   - optional stress advection in the quasi-static predictor (the general
+ *     law of section 2 has -(v.grad) sigma; Eq. 27 drops it): the same ENO
+ *     advection with the mean corner velocity of v^n and the same ghosts as
+ *     the explicit method, added to the rate of Eq. (27).
  *
  * Stencil tables: S[d][a][b] with d = (dz+1)*9 + (dy+1)*3 + (dx+1) for
  * offsets in {-1,0,1}^3, a = output component, b = input component.
@@ -691,35 +695,64 @@ void ora_cell_gradient(int nx, int ny, int nz, double h, const double *v, double
 }
 
 
+double ora_eno(const double *f, double u, double h);
+static double cell_val(const double *f, int nx, int ny, int nz, int kk, int j, int i);
+
 /*
  * Intermediate stress, Eq. (27), with D^pl of the same state:
  *   sigma* = sigma + dt (L sigma + sigma L^T - tr(L) sigma - C:(D^pl sigma0/sbar))
  * with C:X = lam tr(X) I + 2 mu X; sigma0 is traceless, so the plastic term
  * is 2 mu D^pl sigma0 / sbar.  Writes sigma* (6 per cell, same layout as
  * sigma), D^pl and sbar per cell.
+ * With advect != 0 the rate also holds the advection -(u.grad) sigma of the
+ * general constitutive law (section 2, the form Eq. 27 drops): u the mean of
+ * the cell's 8 corner velocities of v^n, the derivatives by ENO (Eq. 33) with
+ * the cell ghosts of the explicit method (linear extrapolation beyond the z
+ * boundaries; x and y wrap).
  */
-void ora_stress_star(int nx, int ny, int nz, double h, double dt, double mu,
-                     const ora_stz *p, const double *v, const double *sig, const double *chi,
-                     double *sig_star, double *dpl, double *sbar_out)
+void ora_stress_star_adv(int nx, int ny, int nz, double h, double dt, double mu,
+                         const ora_stz *p, const double *v, const double *sig, const double *chi,
+                         double *sig_star, double *dpl, double *sbar_out, int advect)
 {
+    static const int comp[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
     long nc = (long)nx * ny * nz;
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; k++)
         for (int j = 0; j < ny; j++)
             for (int i = 0; i < nx; i++) {
                 long q = cell(nx, ny, k, j, i);
-                double s6[6], s[3][3], L[3][3], rate[3][3];
+                double s6[6], s[3][3], L[3][3], rate[3][3], adv[6] = {0, 0, 0, 0, 0, 0};
                 for (int c = 0; c < 6; c++)
                     s6[c] = sig[c * nc + q];
                 sym_full(s6, s);
                 cell_grad(nx, ny, nz, v, h, k, j, i, L);
+                if (advect) {
+                    double u[3] = {0.0, 0.0, 0.0};
+                    for (int a = 0; a < 3; a++)
+                        for (int dk = 0; dk < 2; dk++)
+                            for (int dj = 0; dj < 2; dj++)
+                                for (int di = 0; di < 2; di++)
+                                    u[a] += 0.125 * v[node(nx, ny, nz, a, k + dk, wrap(j + dj, ny),
+                                                           wrap(i + di, nx))];
+                    for (int c = 0; c < 6; c++) {
+                        const double *f = sig + c * nc;
+                        double fx[5], fy[5], fz[5];
+                        for (int m = -2; m <= 2; m++) {
+                            fx[m + 2] = f[cell(nx, ny, k, j, wrap(i + m, nx))];
+                            fy[m + 2] = f[cell(nx, ny, k, wrap(j + m, ny), i)];
+                            fz[m + 2] = cell_val(f, nx, ny, nz, k + m, j, i);
+                        }
+                        adv[c] = u[0] * ora_eno(fx, u[0], h) + u[1] * ora_eno(fy, u[1], h) +
+                                 u[2] * ora_eno(fz, u[2], h);
+                    }
+                }
                 double sb = sbar_of(s);
                 double D = ora_dpl(p, sb, chi[q]);
                 double trL = L[0][0] + L[1][1] + L[2][2];
                 double tr3 = (s[0][0] + s[1][1] + s[2][2]) / 3.0;
                 for (int a = 0; a < 3; a++)
                     for (int b = 0; b < 3; b++) {
-                        double r = -trL * s[a][b];
+                        double r = advect ? -adv[comp[a][b]] - trL * s[a][b] : -trL * s[a][b];
                         for (int c = 0; c < 3; c++)
                             r += L[a][c] * s[c][b] + s[a][c] * L[b][c];
                         if (D > 0.0)
@@ -735,6 +768,13 @@ void ora_stress_star(int nx, int ny, int nz, double h, double dt, double mu,
                 dpl[q] = D;
                 sbar_out[q] = sb;
             }
+}
+
+void ora_stress_star(int nx, int ny, int nz, double h, double dt, double mu,
+                     const ora_stz *p, const double *v, const double *sig, const double *chi,
+                     double *sig_star, double *dpl, double *sbar_out)
+{
+    ora_stress_star_adv(nx, ny, nz, h, dt, mu, p, v, sig, chi, sig_star, dpl, sbar_out, 0);
 }
 
 /* D^pl of a z ghost cell: sigma and chi linearly extrapolated from the two
@@ -904,9 +944,9 @@ void ora_wall_fill(int nx, int ny, int nz, double h, const ora_bc *bc, double t,
  *   6. sigma^{n+1} = sigma* + dt C:D^{n+1}                 Eq. (29)
  * Returns the solver status (0 ok, 5 not converged, 6 non-finite).
  */
-int ora_qs_step(ora_mg *m, double h, double dt, double lam, double mu, const ora_stz *p,
-                const ora_bc *bc, double t, double *v, double *sig, double *chi, double tol,
-                int max_cycles, int *cycles, double *hist)
+int ora_qs_step_adv(ora_mg *m, double h, double dt, double lam, double mu, const ora_stz *p,
+                    const ora_bc *bc, double t, double *v, double *sig, double *chi, double tol,
+                    int max_cycles, int *cycles, double *hist, int advect)
 {
     int nx = m->dims[0][0], ny = m->dims[0][1], nz = m->dims[0][2];
     long nc = (long)nx * ny * nz, nn = 3L * (nz + 1) * ny * nx;
@@ -915,7 +955,7 @@ int ora_qs_step(ora_mg *m, double h, double dt, double lam, double mu, const ora
     double *sbar = (double *)malloc(nc * sizeof(double));
     double *chi_new = (double *)malloc(nc * sizeof(double));
     double *b = (double *)malloc(nn * sizeof(double));
-    ora_stress_star(nx, ny, nz, h, dt, mu, p, v, sig, chi, sig_star, dpl, sbar);
+    ora_stress_star_adv(nx, ny, nz, h, dt, mu, p, v, sig, chi, sig_star, dpl, sbar, advect);
     ora_chi_update(nx, ny, nz, h, dt, p, sig, chi, dpl, sbar, chi_new);
     memcpy(chi, chi_new, nc * sizeof(double));
     ora_wall_fill(nx, ny, nz, h, bc, t + dt, v);
@@ -928,6 +968,14 @@ int ora_qs_step(ora_mg *m, double h, double dt, double lam, double mu, const ora
     free(chi_new);
     free(b);
     return st;
+}
+
+int ora_qs_step(ora_mg *m, double h, double dt, double lam, double mu, const ora_stz *p,
+                const ora_bc *bc, double t, double *v, double *sig, double *chi, double tol,
+                int max_cycles, int *cycles, double *hist)
+{
+    return ora_qs_step_adv(m, h, dt, lam, mu, p, bc, t, v, sig, chi, tol, max_cycles, cycles,
+                           hist, 0);
 }
 
 /* ------------------------------------------------------------------ */
