@@ -87,6 +87,9 @@ def parse():
                          "comparison geometry (64 x 64 x 32)")
     ap.add_argument("--zeta", default="1e4", help="--explicit: comma-separated zeta values")
     ap.add_argument("--t-end", type=float, default=20.0, help="--explicit: end time in t_s")
+    ap.add_argument("--advect", action="store_true",
+                    help="default line with the stress advection of the general law "
+                         "(MG_FLAG_ADVECT_STRESS) on both sides")
     ap.add_argument("--fma-peak", action="store_true",
                     help="measure the FP64 and FP32 FMA rate of the GPU (the FP64 kernels' roofline)")
     return ap.parse_args()
@@ -336,14 +339,14 @@ def traffic_per_sweep(n_nodes):
 
 # --------------------------------------------------------------------- oracle
 
-def oracle_step(w, mg, v, sig, chi, t, tol=TOL):
+def oracle_step(w, mg, v, sig, chi, t, tol=TOL, advect=False):
     """One complete FP64 CPU oracle qs_step in place (predictor, chi update,
     walls, right-hand side, warm-started multigrid solve to tol, stress
     correction), timed end to end; returns (seconds, V-cycles)."""
     import oracle as O
     t0 = time.perf_counter()
     st, cyc, _ = O.qs_step(mg, v, sig, chi, w.h, w.dt, w.lam, w.mu, O.STZ(**w.stz),
-                           O.BC(**w.bc_values()), t, tol=tol, max_cycles=100)
+                           O.BC(**w.bc_values()), t, tol=tol, max_cycles=100, advect=advect)
     dt = time.perf_counter() - t0
     if st != 0:
         raise RuntimeError("oracle qs_step failed with status %d" % st)
@@ -447,7 +450,8 @@ def run_ours(args):
 
     def mk(prec):
         return Context(w.nx, w.ny, w.nz, w.h, I_K(), w.mu, bc=w.bc_values(), stz=w.stz,
-                       precision=prec, max_cycles=100, inner_cycles=args.inner, stream=stream)
+                       precision=prec, max_cycles=100, inner_cycles=args.inner, stream=stream,
+                       flags=binding.MG_FLAG_ADVECT_STRESS if args.advect else 0)
 
     vg = torch.from_numpy(v0).to(dev)
     sg = torch.from_numpy(s0).to(dev)
@@ -546,7 +550,7 @@ def run_ours(args):
         import oracle as O
         vs, ss_, cs_ = (a.cpu().numpy() for a in snap[:3])
         mg = O.MG(w.nx, w.ny, w.nz, w.lam, w.mu)
-        t_cpu, cyc_cpu = oracle_step(w, mg, vs, ss_, cs_, snap[3])
+        t_cpu, cyc_cpu = oracle_step(w, mg, vs, ss_, cs_, snap[3], advect=args.advect)
         mg.close()
         vg.copy_(snap[0])
         sg.copy_(snap[1])
@@ -572,7 +576,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycles in f64 refinement",
         "data": "synthetic (seeded fields of the paper's recipes)",
         "config": config(w, {"precision": "mixed", "inner_cycles": args.inner,
-                             "parallelism": "replicas" if ws > 1 else "single GPU"}),
+                             "parallelism": "replicas" if ws > 1 else "single GPU",
+                             **({"stress_advection": "ENO, MG_FLAG_ADVECT_STRESS"}
+                                if args.advect else {})}),
         "solve": {"cycles_per_solve": cyc / K, "outer_per_solve": outer / K,
                   "worst_rel_resid": worst},
         "fp64": ({"value": lock["fp64_s_per_step"], "unit": UNIT, "steps": lock["steps"],

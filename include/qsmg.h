@@ -58,8 +58,10 @@ enum {
     MG_FLAG_COLOUR_PASSES = 1, /* FP32 sweeps: one launch per colour */
     MG_FLAG_NO_GRAPH = 2,      /* FP32 inner cycles: plain launches, no CUDA graph */
     MG_FLAG_FUSED_SWEEP = 4,   /* finest FP32 sweeps: both k-parities in one launch */
-    MG_FLAG_UNFUSED_TRANSFERS = 8 /* finest FP32 residual and restriction as
-                                     separate passes */
+    MG_FLAG_UNFUSED_TRANSFERS = 8, /* finest FP32 residual and restriction as
+                                      separate passes */
+    MG_FLAG_ADVECT_STRESS = 16     /* qs_step / qs_run / qs_stress_predict: add the
+                                      stress advection -(v.grad) sigma to sigma* */
 };
 enum { MG_HIST = 128 };
 
@@ -114,7 +116,13 @@ typedef struct {
  *                 kept for comparison); MG_FLAG_UNFUSED_TRANSFERS runs the
  *                 finest-level FP32 residual and its restriction as two passes
  *                 with the residual stored instead of one fused pass (kept
- *                 for comparison).
+ *                 for comparison); MG_FLAG_ADVECT_STRESS adds to the
+ *                 intermediate stress of Eq. (27) the advection term
+ *                 -(v.grad) sigma of the general constitutive law (section 2),
+ *                 sigma* -= dt (u.grad) sigma^n with u the mean of each cell's
+ *                 8 corner velocities of v^n and ENO derivatives (Eq. 33),
+ *                 cell fields extrapolated linearly two layers beyond the z
+ *                 boundaries (the reverse-mode entry points reject it).
  */
 typedef struct {
     int precision;

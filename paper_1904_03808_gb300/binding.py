@@ -23,6 +23,7 @@ MG_FLAG_COLOUR_PASSES = 1
 MG_FLAG_NO_GRAPH = 2
 MG_FLAG_FUSED_SWEEP = 4
 MG_FLAG_UNFUSED_TRANSFERS = 8
+MG_FLAG_ADVECT_STRESS = 16
 MG_HIST = 128
 
 

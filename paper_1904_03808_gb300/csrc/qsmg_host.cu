@@ -1050,6 +1050,7 @@ mg_status qs_run(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol
     }
     if (nsteps == 0) return MG_OK;
     const StepParams p = step_params(ctx, dt);
+    const bool advect = (ctx->opts.flags & MG_FLAG_ADVECT_STRESS) != 0;
     CK(stress_predict(p, state->v, state->sigma, state->chi, ctx->sig_star, ctx->dpl, ctx->sbar,
                       ctx->st));
     mg_status s = MG_OK;
@@ -1058,6 +1059,8 @@ mg_status qs_run(mg_ctx *ctx, qs_state *state, int nsteps, double dt, double tol
         if (n > 0)
             CK(correct_predict(p, state->v, ctx->sig_star, state->sigma, ctx->chi_tmp, state->chi,
                                ctx->dpl, ctx->sbar, ctx->st));
+        // optional -(u.grad) sigma^n in sigma* (state->sigma and v hold step n)
+        if (advect) CK(stress_advect(p, state->v, state->sigma, ctx->sig_star, ctx->st));
         CK(chi_update(p, state->sigma, state->chi, ctx->dpl, ctx->sbar, ctx->chi_tmp, ctx->st));
         CK(wall_fill(wall_params(ctx, state->t + dt), state->v, ctx->st));
         CK(div_rhs(p, ctx->sig_star, ctx->rhs, ctx->st));
@@ -1300,7 +1303,10 @@ static mg_status step_arg(mg_ctx *ctx) {
 mg_status qs_stress_predict(mg_ctx *ctx, const double *v, const double *sigma, const double *chi,
                             double dt, double *sigma_star, double *dpl, double *sbar) {
     CKS(step_arg(ctx));
-    CK(stress_predict(step_params(ctx, dt), v, sigma, chi, sigma_star, dpl, sbar, ctx->st));
+    const StepParams p = step_params(ctx, dt);
+    CK(stress_predict(p, v, sigma, chi, sigma_star, dpl, sbar, ctx->st));
+    if (ctx->opts.flags & MG_FLAG_ADVECT_STRESS)
+        CK(stress_advect(p, v, sigma, sigma_star, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return MG_OK;
 }
@@ -1352,6 +1358,10 @@ mg_status qs_step_adjoint(mg_ctx *ctx, const qs_state *state, double dt, double 
     }
     if (!ctx->has_stz) {
         set_err("qs_step_adjoint: context was set up without stz parameters");
+        return MG_ERR_ARG;
+    }
+    if (ctx->opts.flags & MG_FLAG_ADVECT_STRESS) {
+        set_err("qs_step_adjoint: reverse mode has no adjoint of the stress advection");
         return MG_ERR_ARG;
     }
     const Dims &d = ctx->L[0];
@@ -1450,6 +1460,10 @@ mg_status work_args(mg_ctx *ctx, const void *state, int nsteps, double dt, int c
     }
     if (!ctx->has_stz || !ctx->has_bc) {
         set_err("%s: context was set up without stz/bc parameters", who);
+        return MG_ERR_ARG;
+    }
+    if (ctx->opts.flags & MG_FLAG_ADVECT_STRESS) {
+        set_err("%s: reverse mode has no adjoint of the stress advection", who);
         return MG_ERR_ARG;
     }
     return MG_OK;

@@ -237,6 +237,9 @@ cudaError_t div_rhs(const StepParams &p, const double *sig_star, double *b, cuda
 // sigma = sigma* + dt C:D(v); if chi_src is given also chi_dst = chi_src
 cudaError_t stress_correct(const StepParams &p, const double *v, const double *sig_star,
                            double *sig, const double *chi_src, double *chi_dst, cudaStream_t s);
+// sigma* -= dt (u.grad) sigma (ENO, Eq. 33; u the mean corner velocity of v)
+cudaError_t stress_advect(const StepParams &p, const double *v, const double *sig,
+                          double *sig_star, cudaStream_t s);
 // Eq. (29) of one step fused with Eq. (27) of the next (same v): sig_star is
 // sigma* of the finished step on entry, of the next step on return
 cudaError_t correct_predict(const StepParams &p, const double *v, double *sig_star, double *sig,

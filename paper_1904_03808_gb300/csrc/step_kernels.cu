@@ -387,6 +387,47 @@ __device__ __forceinline__ double eno_d(double fm2, double fm1, double f0, doubl
     return (fp1 - fm1) * inv2h;
 }
 
+// (u.grad) sigma_n at cell (i, j, k) for the 6 stored components: ENO
+// derivatives (Eq. 33) along x and y (wrapping) and z, where cell fields two
+// layers beyond the z boundaries are extrapolated linearly from the two
+// layers next to them; u is the cell's advecting velocity
+__device__ __forceinline__ void stress_advection(const StepParams &p,
+                                                 const double *__restrict__ sig, long nc, int i,
+                                                 int j, int k, const double (&u)[3],
+                                                 double inv2h, double (&adv)[6]) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const long pl = (long)nx * ny;
+    int ix[5], jy[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) {
+        int a = i + m - 2, b = j + m - 2;
+        ix[m] = a < 0 ? a + nx : (a >= nx ? a - nx : a);
+        jy[m] = b < 0 ? b + ny : (b >= ny ? b - ny : b);
+    }
+#pragma unroll
+    for (int n = 0; n < 6; n++) {
+        const double *f = sig + n * nc;
+        double fx[5], fy[5], fz[5];
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            fx[m] = f[(long)k * pl + (long)j * nx + ix[m]];
+            fy[m] = f[(long)k * pl + (long)jy[m] * nx + i];
+            const int kk = k + m - 2;
+            const long col = (long)j * nx + i;
+            if (kk < 0)
+                fz[m] = f[col] + kk * (f[pl + col] - f[col]);
+            else if (kk > nz - 1)
+                fz[m] = f[(long)(nz - 1) * pl + col] +
+                        (kk - (nz - 1)) * (f[(long)(nz - 1) * pl + col] - f[(long)(nz - 2) * pl + col]);
+            else
+                fz[m] = f[(long)kk * pl + col];
+        }
+        adv[n] = u[0] * eno_d(fx[0], fx[1], fx[2], fx[3], fx[4], u[0], inv2h) +
+                 u[1] * eno_d(fy[0], fy[1], fy[2], fy[3], fy[4], u[1], inv2h) +
+                 u[2] * eno_d(fz[0], fz[1], fz[2], fz[3], fz[4], u[2], inv2h);
+    }
+}
+
 // Eq. (25) at cell centres: sigma' = sigma + dt (-(u.grad) sigma + L sigma +
 // sigma L^T - tr(L) sigma + C:(D - D^pl sigma0 / sbar)), L the Eq. (31)
 // gradient of v, u the mean of the cell's 8 corner velocities; the ENO
@@ -417,37 +458,10 @@ __global__ void k_explicit_stress(StepParams p, StzConst c, const double *__rest
         u[a] = 0.125 * (((c000 + c001) + (c010 + c011)) + ((c100 + c101) + (c110 + c111)));
     }
     const long q = (long)k * pl + (long)j * nx + i;
-    int ix[5], jy[5];
-#pragma unroll
-    for (int m = 0; m < 5; m++) {
-        int a = i + m - 2, b = j + m - 2;
-        ix[m] = a < 0 ? a + nx : (a >= nx ? a - nx : a);
-        jy[m] = b < 0 ? b + ny : (b >= ny ? b - ny : b);
-    }
     double s6[6], adv[6];
 #pragma unroll
-    for (int n = 0; n < 6; n++) {
-        const double *f = sig + n * nc;
-        s6[n] = f[q];
-        double fx[5], fy[5], fz[5];
-#pragma unroll
-        for (int m = 0; m < 5; m++) {
-            fx[m] = f[(long)k * pl + (long)j * nx + ix[m]];
-            fy[m] = f[(long)k * pl + (long)jy[m] * nx + i];
-            const int kk = k + m - 2;
-            const long col = (long)j * nx + i;
-            if (kk < 0)
-                fz[m] = f[col] + kk * (f[pl + col] - f[col]);
-            else if (kk > nz - 1)
-                fz[m] = f[(long)(nz - 1) * pl + col] +
-                        (kk - (nz - 1)) * (f[(long)(nz - 1) * pl + col] - f[(long)(nz - 2) * pl + col]);
-            else
-                fz[m] = f[(long)kk * pl + col];
-        }
-        adv[n] = u[0] * eno_d(fx[0], fx[1], fx[2], fx[3], fx[4], u[0], inv2h) +
-                 u[1] * eno_d(fy[0], fy[1], fy[2], fy[3], fy[4], u[1], inv2h) +
-                 u[2] * eno_d(fz[0], fz[1], fz[2], fz[3], fz[4], u[2], inv2h);
-    }
+    for (int n = 0; n < 6; n++) s6[n] = sig[n * nc + q];
+    stress_advection(p, sig, nc, i, j, k, u, inv2h, adv);
     const double S[3][3] = {{s6[0], s6[5], s6[4]}, {s6[5], s6[1], s6[3]}, {s6[4], s6[3], s6[2]}};
     const double sb = sbar_of(s6);
     const double inv_sb = sb > 0.0 ? 1.0 / sb : 0.0;
@@ -468,6 +482,35 @@ __global__ void k_explicit_stress(StepParams p, StzConst c, const double *__rest
     }
     dpl[q] = D;
     sbar_out[q] = sb;
+}
+
+// the stress advection of the general constitutive law (section 2), which
+// Eq. (27) drops, as an option of the quasi-static step: sigma* -= dt (u.grad)
+// sigma^n, u the mean of the cell's 8 corner velocities of v^n (the
+// explicit method's advection, Eq. 33 and its ghosts)
+__global__ void k_stress_advect(StepParams p, const double *__restrict__ v,
+                                const double *__restrict__ sig, double *__restrict__ sig_star,
+                                long nc) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    int i, j, k;
+    if (!cell_ijk(nx, ny, i, j, k)) return;
+    const long pl = (long)nx * ny, cs = (long)(nz + 1) * pl;
+    const int i1 = i + 1 < nx ? i + 1 : 0, j1 = j + 1 < ny ? j + 1 : 0;
+    double u[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double *g = v + a * cs;
+        const long b0 = (long)k * pl, b1 = b0 + pl, r0 = (long)j * nx, r1 = (long)j1 * nx;
+        u[a] = 0.125 * (((g[b0 + r0 + i] + g[b0 + r0 + i1]) + (g[b0 + r1 + i] + g[b0 + r1 + i1])) +
+                        ((g[b1 + r0 + i] + g[b1 + r0 + i1]) + (g[b1 + r1 + i] + g[b1 + r1 + i1])));
+    }
+    double adv[6], ss[6];
+    stress_advection(p, sig, nc, i, j, k, u, 0.5 / p.h, adv);
+    const long q = (long)k * pl + (long)j * nx + i;
+#pragma unroll
+    for (int n = 0; n < 6; n++) ss[n] = sig_star[n * nc + q];
+#pragma unroll
+    for (int n = 0; n < 6; n++) sig_star[n * nc + q] = ss[n] - p.dt * adv[n];
 }
 
 // Eq. (24) at interior corners (k = 1 .. nz-1):
@@ -582,6 +625,14 @@ cudaError_t stress_correct(const StepParams &p, const double *v, const double *s
     const long nc = (long)p.nx * p.ny * p.nz;
     k_stress_correct<<<cell_grid(p.nx, p.ny, (p.nz + kCellChunk - 1) / kCellChunk), kBlock, 0, s>>>(p, v, sig_star, sig, chi_src,
                                                                     chi_dst, nc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t stress_advect(const StepParams &p, const double *v, const double *sig,
+                          double *sig_star, cudaStream_t s) {
+    const long nc = (long)p.nx * p.ny * p.nz;
+    k_stress_advect<<<cell_grid(p.nx, p.ny, p.nz), kBlock, 0, s>>>(p, v, sig, sig_star, nc);
     count_launch();
     return cudaGetLastError();
 }
