@@ -13,7 +13,8 @@
 //                each tile are copied into shared memory with cp.async while
 //                the other CTAs on the SM compute; templated on the operator
 //                (FineRowsOp, CoarseRowsOp) and, with RES, computing the
-//                residual b - A x instead of a sweep phase;
+//                residual b - A x instead of a sweep phase (with RR as well,
+//                restricting it in x and y on the fly instead of storing it);
 //   k_gs_rows    one CTA per tile, operands loaded straight into registers,
 //                for the other finest rows of up to 512 nodes.
 // Both compute every node from the same neighbour values as the sequential

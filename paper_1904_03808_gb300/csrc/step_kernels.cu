@@ -1,6 +1,9 @@
 // step_kernels.cu -- pointwise kernels of the quasi-static projection step
 // (section 3.3): stress predictor with the STZ rate, effective temperature,
-// right-hand side of the projection system, stress correction, wall fill.
+// right-hand side of the projection system, stress correction (alone, or
+// fused with the next step's predictor), wall fill, and the optional stress
+// advection; the explicit method of section 3.2 (ENO advection, Eq. 33); and
+// the adjoint kernels of the reverse mode.
 //
 // Cell arrays (nz, ny, nx); stress (6, nz, ny, nx) in the order xx, yy, zz,
 // yz, xz, xy; corner arrays (3, nz+1, ny, nx).  x and y are periodic.
