@@ -310,7 +310,11 @@ cudaError_t rows_phase(const Dims &d, const Fine<float> &f, const float *b, cons
 // third CTA per SM: 10-17% slower); a cyclic plane-major tile order (27%
 // fewer DRAM bytes, 18% slower: it loses the z-plane reuse); one thread per
 // node component instead of per column pair (35% slower); natural instead of
-// parity-split column order (8% slower).
+// parity-split column order (8% slower); the prolongation x += T xc folded
+// into the first post-sweep, each tile adding it to its copied input rows
+// (the two launches took 323 + 158 us against 175 us for the plain sweep
+// plus 146 us for the separate prolongation: every window row waits on its
+// coarse loads from L2, with no registers or shared memory left to prefetch).
 constexpr int kPersTY = 6;
 constexpr int kPersR = kPersTY + 3;
 constexpr int kPersMinBlocks = 2;  // resident CTAs per SM at nx = 256 (more for shorter rows)
